@@ -1,0 +1,44 @@
+"""Synthetic workloads of the space-time MLMC monodomain path: parameters only.
+
+This module holds no arithmetic of the method.  Each workload is the shape
+and parameter set of one benchmark configuration; both the CUDA path and the
+CPU oracle are driven from these dictionaries by the tests and the benchmark.
+
+Problem (arXiv:1911.06066, Sec. 2.1 / 2.2 in the variant the workloads fix):
+    u_t = div(D grad u) + c u (1-u) (u-a)      on a box, Neumann boundary,
+    D = s_t I + (s_l - s_t) f f^T,  s_l = s_l0 exp(Z),  f = (cos th, sin th, 0),
+    Z = sum_k sqrt(lam_k) phi_k xi_k  (separable exponential covariance),
+    u(x, 0) = 1 inside the ball |x - x_c| < stim_r, else 0,
+    QoI: activation time, the first t with u >= 1/2 (linear in t).
+Level l refines every axis and the time grid by 2^l.
+"""
+
+# Reaction, conductivity, stimulus and end time shared by every workload.
+COMMON = dict(T=5.0, c=100.0, a=0.1, s_t=2.5e-4, s_l0=1e-3, stim_r=0.1,
+              stim_c=(0.0, 0.0, 0.0), sigma2=0.04)
+
+MC2D_32 = dict(
+    name="mc2d_32x32_m64_M16",
+    dim=2, L=(1.0, 1.0), n0=(32, 32), m0=64, levels=1,
+    theta0=30.0, theta1=30.0, ell=0.2, M=16,
+    N=[16], seed=0, **COMMON)
+
+MLMC2D_3LVL = dict(
+    name="mlmc2d_3lvl_32-128_m64-256_M64",
+    dim=2, L=(1.0, 1.0), n0=(32, 32), m0=64, levels=3,
+    theta0=30.0, theta1=30.0, ell=0.1, M=64,
+    N=[512, 128, 32], seed=0, **COMMON)
+
+SLAB3D_4LVL = dict(
+    name="mlmc3d_4lvl_32x32x8-256x256x64_m32-256_M256",
+    dim=3, L=(1.0, 1.0, 0.25), n0=(32, 32, 8), m0=32, levels=4,
+    theta0=-60.0, theta1=60.0, ell=0.1, M=256,
+    N=[256, 64, 16, 4], seed=0, **COMMON)
+
+WORKLOADS = {w["name"]: w for w in (MC2D_32, MLMC2D_3LVL, SLAB3D_4LVL)}
+
+
+def level_shape(w, l):
+    """(cells per axis, time steps) of level l of workload w."""
+    f = 2 ** l
+    return tuple(n * f for n in w["n0"]), w["m0"] * f
