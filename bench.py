@@ -1,0 +1,276 @@
+"""Benchmark of the space-time MLMC monodomain path on GB300.
+
+One step = one complete MLMC estimate of the mean activation map of the
+3-level 2D workload (32^2/64^2/128^2 Q1 grids, 64/128/256 implicit-Euler
+steps, 64 KL modes, N_l = 512/128/32 level pairs): xi, KL fields, both solves
+of every pair, activation maps, level differences, accumulation and the
+estimate, all through ``mlmc_run`` of the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                    [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is device time per estimate (CUDA events on
+the launching stream, L2 flushed between steps); ``e2e`` is the wall time of
+the same public call with host inputs and host outputs; ``roofline`` is for
+the per-sample solve kernel, from CUDA events around its launches inside the
+timed region and the iteration counts it reports; ``cpu_baseline`` times the
+oracle on this host's cores on a bounded sample of the same workload.
+``--impl reference`` times the oracle alone as the reference arm.
+"""
+import argparse
+import concurrent.futures
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-RMSE eps (s) for MLMC mean activation map; stencil HBM GB/s; p99 latency"
+# FP64 FMA throughput measured on this GB300 with independent FMA chains
+# (152 SMs; 2 FP64 FMA per clock per SM nominally = 1.26 TFLOP/s at 2.07 GHz).
+FP64_PEAK_TFLOPS = 1.01
+# Algorithmic flops per node of one CG iteration (9-coupling stencil + Hessian
+# diagonal 20, two dots 4, four vector updates 7) and of one Newton iteration
+# (residual 25, Hessian diagonal and Jacobi inverse 13, CG start 4, update 3).
+FLOP_CG_NODE = 31
+FLOP_NEWTON_NODE = 45
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample_cost(w, pairs, seed=1000, threads=None):
+    """Single-thread seconds per level pair, measured on `pairs[l]` pairs of each
+    level run concurrently on `threads` host threads (the C oracle releases the GIL)."""
+    import oracle as O
+    from paper_1911_06066_gb300 import workloads as W
+    threads = threads or (os.cpu_count() or 1)
+    levels = []
+    for l in range(w["levels"]):
+        n, m = W.level_shape(w, l)
+        levels.append(O.make_level(w["dim"], n, m, w["L"], w["T"], w["c"], w["a"], w["s_t"],
+                                   w["s_l0"], w["theta0"], w["theta1"], w["stim_r"], w["stim_c"]))
+    jobs = [(l, i) for l in range(w["levels"]) for i in range(pairs[l])]
+    # longest first so the pool drains evenly
+    jobs.sort(key=lambda j: -j[0])
+
+    def one(job):
+        l, i = job
+        t0 = time.perf_counter()
+        O.sample_pair(levels[l], levels[l - 1] if l else None, levels[0], w["sigma2"], w["ell"],
+                      w["M"], seed, l, i)
+        return l, time.perf_counter() - t0
+
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(one, jobs))
+    wall = time.perf_counter() - t0
+    per = []
+    for l in range(w["levels"]):
+        ts = [t for ll, t in res if ll == l]
+        per.append(sum(ts) / len(ts) if ts else 0.0)
+    return per, wall, min(threads, len(jobs))
+
+
+def cpu_estimate_seconds(w, per_pair, cores):
+    """All-core time of one full estimate: sum_l N_l C_l / cores."""
+    return sum(n * c for n, c in zip(w["N"], per_pair)) / cores
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, w):
+    """The oracle (CPU, FP64) as the reference arm: each step times a bounded
+    sample of level pairs on all host cores and extrapolates to one estimate."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    sample = [16, 4, 1]
+    for _ in range(args.warmup):
+        oracle_sample_cost(w, [2, 0, 0])
+    vals = []
+    for k in range(args.steps):
+        per, wall, used = oracle_sample_cost(w, sample, seed=2000 + k, threads=cores)
+        vals.append(cpu_estimate_seconds(w, per, cores))
+    v = sum(vals) / len(vals)
+    desc = "L0/L1/L2 pairs %s per step, single-thread time per pair x N_l / %d cores" % (sample, cores)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "N_l": w["N"]},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # CPU baseline first: host threads only, before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sample = [32, 8, 2]
+        per, wall, used = oracle_sample_cost(w, sample, threads=cores)
+        cpu = {"value": cpu_estimate_seconds(w, per, cores), "unit": "s", "cores": cores,
+               "kind": "oracle",
+               "sample": "level pairs %s of the workload on %d host threads (%.1f s wall); "
+                         "single-thread s/pair %s, extrapolated to N_l=%s on %d cores"
+                         % (sample, used, wall, [round(x, 4) for x in per], w["N"], cores)}
+
+    from __graft_entry__ import build
+    build()
+    from paper_1911_06066_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = B.MLMC_PREC_MIXED if args.precision == "mixed" else B.MLMC_PREC_FP64
+    ctx = B.Context(B.make_config(w, prec))
+    seed = 1 + rank      # disjoint streams per rank: each rank runs its own estimate
+    batch = max(w["N"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        ctx.run(w["N"], seed=seed, batch=batch)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    dev_ms, wall_s, solve_ms, cg_ni, nw_ni, launches, rmse = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, []
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush (512 MB > 126 MB L2) outside the timed span
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        res = ctx.run(w["N"], seed=seed, batch=batch)     # host in, host out (synchronising)
+        e1.record(stream)
+        t1 = time.perf_counter()
+        torch.cuda.synchronize()
+        dev_ms += e0.elapsed_time(e1)
+        wall_s += t1 - t0
+        st = res["stats"]
+        solve_ms += st["solve_ms"]
+        cg_ni += st["cg_node_iters"]
+        nw_ni += st["newton_node_iters"]
+        launches += st["launches"]
+        rmse.append(res["rmse"])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    ms = dev_ms / args.steps
+    e2e_s = wall_s / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = t[0].item(), t[1].item()
+    if rank != 0:
+        return
+    flops = FLOP_CG_NODE * cg_ni + FLOP_NEWTON_NODE * nw_ni
+    achieved = flops / (solve_ms * 1e-3) / 1e12 if solve_ms > 0 else 0.0
+    L = w["levels"]
+    n0 = (w["n0"][0] + 1) * (w["n0"][1] + 1) * ((w["n0"][2] + 1) if w["dim"] == 3 else 1)
+    d2h = 8 * (2 * n0 + 2 * L * n0 + L + 2) + 8 * 5
+    out = {
+        "metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == B.MLMC_PREC_FP64 else "f64+f32 (FP32 CG inside FP64 Newton)",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "N_l": w["N"], "grids": "32^2/64^2/128^2",
+                   "steps_per_level": [64, 128, 256], "kl_modes": w["M"],
+                   "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+                   "rmse_achieved": statistics.mean(rmse), "parallelism": "samples per thread block"},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * L,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "solve_kernel (per-sample Newton-CG sweep)",
+                     "peak_source": "FP64 FMA-chain probe on GB300 (measured)",
+                     "solve_share": (solve_ms / args.steps) / ms if ms > 0 else None},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    from paper_1911_06066_gb300 import workloads as W
+    w = W.MLMC2D_3LVL
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

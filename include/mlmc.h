@@ -1,0 +1,204 @@
+/*
+ * mlmc.h -- C ABI of the GB300 space-time multilevel Monte Carlo library for
+ * the stochastic monodomain equation (arXiv:1911.06066).
+ *
+ * Problem (Sec. 2.1, Eq. monodomain and Eq. ionic_term; Sec. 2.2,
+ * Eq. KL-expansion), in the variant this library implements:
+ *     u_t = div(D grad u) + c u (1-u) (u-a)   on a box, Neumann boundary,
+ *     D   = s_t I + (s_l - s_t) f f^T,  s_l = s_l0 exp(Z),  f = (cos th, sin th, 0),
+ *     Z   = sum_k sqrt(lam_k) phi_k(x) xi_k,  xi_k ~ N(0,1) (Philox4x32-10),
+ *     u(x,0) = 1 inside the ball |x - x_c| < stim_r, else 0,
+ * discretised by Q1 elements with lumped mass and implicit Euler (the block
+ * lower-bidiagonal space-time system of Sec. 3.2, Eq. system_C, with the
+ * reaction of Sec. 3.3, Eq. mono_disc), solved by Newton.  The quantity of
+ * interest is the activation time (first t with u >= 1/2, linear in t).  Its
+ * mean and variance are estimated by MC / MLMC (Sec. 2.2, Eq. MC-estimator,
+ * Eq. MLMC-estimator).
+ *
+ * Conventions for every call:
+ *   - "device" pointers are CUDA device memory of the current device, owned by
+ *     the caller; "host" pointers are host memory owned by the caller.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     calls are asynchronous on it unless stated otherwise.
+ *   - every call returns an mlmc_status; on error nothing is enqueued and
+ *     mlmc_last_error(ctx) describes the failure.  No call aborts the process.
+ *   - a context is not thread-safe; use one per host thread.
+ *   - node arrays are ordered x fastest, then y, then z; cell arrays likewise.
+ *     Level l has n0[d] * 2^l cells per axis and m0 * 2^l time steps.
+ */
+#ifndef MLMC_H
+#define MLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLMC_MAX_LEVELS 8
+
+typedef enum {
+  MLMC_OK = 0,
+  MLMC_ERR_ARG = -1,          /* invalid argument or configuration            */
+  MLMC_ERR_OOM = -2,          /* device allocation failed                      */
+  MLMC_ERR_NOT_CONVERGED = -3,/* a sample's Newton iteration did not converge  */
+  MLMC_ERR_TIMEOUT = -4,      /* a bounded device wait ran out                 */
+  MLMC_ERR_CUDA = -5,         /* a CUDA runtime call failed                    */
+  MLMC_ERR_WORKSPACE = -6     /* workspace missing, too small or misaligned    */
+} mlmc_status;
+
+typedef enum {
+  MLMC_PREC_FP64 = 0,   /* every step in FP64                                       */
+  MLMC_PREC_MIXED = 1   /* FP32 Krylov inner solves; FP64 residual, update, QoI     */
+} mlmc_precision;
+
+/* Problem and solver configuration (plain data, copied by mlmc_create). */
+typedef struct {
+  int dim;               /* 2 or 3                                                  */
+  int n_levels;          /* 1 .. MLMC_MAX_LEVELS                                     */
+  int n0[3];             /* level-0 cells per axis (n0[2] ignored in 2D)             */
+  int m0;                /* level-0 implicit-Euler steps                            */
+  double L[3];           /* box extents                                              */
+  double T;              /* end time                                                 */
+  double c, a;           /* reaction c u (1-u)(u-a)                                  */
+  double s_t, s_l0;      /* transverse / longitudinal conductivity                   */
+  double theta0_deg;     /* fiber angle; in 3D it varies linearly in z from          */
+  double theta1_deg;     /*   theta0 at z = 0 to theta1 at z = L[2]                  */
+  double stim_r;         /* stimulus radius and centre                               */
+  double stim_c[3];
+  double kl_sigma2;      /* KL variance, correlation length, number of modes         */
+  double kl_ell;
+  int kl_modes;
+  int precision;         /* mlmc_precision                                           */
+  double newton_tol;     /* stop when max |Newton correction| <= newton_tol          */
+  int newton_max;        /* Newton iterations per time step                          */
+  double lin_rtol;       /* CG relative tolerance (FP64 inner solves)                */
+  int lin_max;           /* CG iterations per Newton step                            */
+} mlmc_config;
+
+/* Per-sample solver report, written by the solve calls (device array). */
+typedef struct {
+  int32_t status;        /* MLMC_OK or MLMC_ERR_NOT_CONVERGED                        */
+  int32_t failed_step;   /* first step that did not converge (0 if none)             */
+  int32_t newton_iters;  /* summed over the time steps                               */
+  int32_t cg_iters;      /* summed over all Newton steps                             */
+  int32_t truncations;   /* CG runs stopped at negative curvature                    */
+  int32_t halvings;      /* line-search step halvings                                */
+  int32_t max_newton;    /* largest Newton count of one step                         */
+  int32_t pad;
+} mlmc_sample_info;
+
+typedef struct mlmc_ctx mlmc_ctx;
+
+/* Create a context for one configuration on the current CUDA device.
+ * Builds the KL mode table (Sec. 2.2, Eq. KL-expansion-deterministic) on the
+ * host and copies it and the level descriptors to the device (small, owned by
+ * the context).  *out is NULL on failure. */
+mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out);
+void mlmc_destroy(mlmc_ctx* ctx);
+/* Description of the last failure of this context (or of mlmc_create when ctx
+ * is NULL); never NULL. */
+const char* mlmc_last_error(const mlmc_ctx* ctx);
+
+/* Sizes of level l: nodes, cells and time steps (host outputs, any may be NULL). */
+mlmc_status mlmc_level_info(const mlmc_ctx* ctx, int level, int64_t* nodes, int64_t* cells,
+                            int32_t* steps);
+
+/* Bytes of device workspace needed by mlmc_solve / mlmc_sample_level for n
+ * samples of level l (256-byte aligned pointer required). */
+mlmc_status mlmc_workspace_bytes(const mlmc_ctx* ctx, int level, int n, size_t* bytes);
+
+/* Row a1 -- xi for n samples (Sec. 2.2: the psi_k / y_k of the KL expansion,
+ * here standard normal): Philox4x32-10 (Salmon et al., SC'11) with
+ *   counter = (mode pair j, lo32(id), hi32(id), level), key = (lo32(seed), hi32(seed)),
+ * and Box-Muller with correctly rounded operations only, so that the values
+ * are bit-reproducible.  ids: device [n]; xi: device [n][kl_modes]. */
+mlmc_status mlmc_xi(mlmc_ctx* ctx, uint64_t seed, int level, const uint64_t* ids, int n,
+                    double* xi, void* stream);
+
+/* Row a2 -- truncated KL field on the cell centroids of grid level l
+ * (Sec. 2.2, Eq. KL-expansion-deterministic):
+ *   Z[s][cell] = sum_k sqrt(lam_k) phi_k(centroid) xi[s][k].
+ * xi: device [n][kl_modes]; Z: device [n][cells_l]. */
+mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
+                          void* stream);
+
+/* Rows a3-a8 -- per-sample solve on grid level l: conductivity from Z, Q1
+ * assembly, implicit Euler over all m_l steps with Newton (Sec. 3.3, 3.5),
+ * activation times.
+ *   Z:      device [n][cells_l]            (input)
+ *   t_act:  device [n][nodes_l]            (output; T where never activated)
+ *   slab:   device [n][m_l + 1][nodes_l] or NULL (output: every time slice)
+ *   info:   device [n] or NULL             (output)
+ *   ws:     device workspace of mlmc_workspace_bytes(ctx, l, n) bytes.
+ * A sample that does not converge is reported in info[s].status and does not
+ * affect the others. */
+mlmc_status mlmc_solve(mlmc_ctx* ctx, int level, const double* Z, int n, double* t_act,
+                       double* slab, mlmc_sample_info* info, void* ws, size_t ws_bytes,
+                       void* stream);
+
+/* Row a4 over the whole slab -- the all-at-once space-time residual of
+ * Eq. mono_disc (implicit-Euler blocks), one launch for all n samples:
+ *   F[s][k-1] = (M/dt)(u_k - u_{k-1}) + K u_k - M c u_k(1-u_k)(u_k-a),  k = 1..m_l
+ *   res_max[s] = max_{k,i} |F[s][k-1][i]| / M_i.
+ * slab: device [n][m_l+1][nodes_l]; Z as for mlmc_solve; F: device
+ * [n][m_l][nodes_l] or NULL; res_max: device [n] or NULL. */
+mlmc_status mlmc_slab_residual(mlmc_ctx* ctx, int level, const double* Z, const double* slab,
+                               int n, double* F, double* res_max, void* stream);
+
+/* Row a8 -- activation times from a stored slab (first crossing of 1/2,
+ * linear in time; 0 where u_0 >= 1/2; T where never crossed).
+ * slab: device [n][m_l+1][nodes_l]; t_act: device [n][nodes_l]. */
+mlmc_status mlmc_activation(mlmc_ctx* ctx, int level, const double* slab, int n, double* t_act,
+                            void* stream);
+
+/* Rows a1-a9 -- n level-l sample pairs (Sec. 2.2, Eq. MLMC-estimator): one xi
+ * per pair (counter level = l), the fine (l) and coarse (l-1) problems solved
+ * with that xi, activation maps injected onto the level-0 vertices and
+ *   y[s]  = t_l - t_{l-1},   y2[s] = t_l^2 - t_{l-1}^2     (t_{-1} = 0).
+ * ids: device [n]; y, y2: device [n][nodes_0]; t_fine: device [n][nodes_l] or
+ * NULL; t_coarse: device [n][nodes_{l-1}] or NULL; info: device [2n] or NULL
+ * (fine reports first, then coarse); ws: mlmc_workspace_bytes(ctx, l, n). */
+mlmc_status mlmc_sample_level(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* ids,
+                              int n, double* y, double* y2, double* t_fine, double* t_coarse,
+                              mlmc_sample_info* info, void* ws, size_t ws_bytes, void* stream);
+
+/* Row a10 -- merge a batch of n pair differences into the context's per-level
+ * running estimates (Welford / Chan et al. pairwise update, FP64, fixed order).
+ * y, y2: device [n][nodes_0]. */
+mlmc_status mlmc_accumulate(mlmc_ctx* ctx, int level, const double* y, const double* y2, int n,
+                            void* stream);
+/* Clear every level's running estimates. */
+mlmc_status mlmc_reset(mlmc_ctx* ctx, void* stream);
+
+/* Row a10 -- the estimates (host outputs, any may be NULL; synchronises the
+ * stream).  mean, var: [nodes_0] = sum_l mean(Y_l) and the second-moment
+ * telescoping sum minus mean^2 (clipped at 0); mean_l, var_l: [n_levels][nodes_0];
+ * V_l: [n_levels] = sum_i w_i Var(Y_l)_i with w the level-0 lumped mass;
+ * N_l: [n_levels]; rmse: sqrt(sum V_l/N_l + bias^2), bias = ||mean(Y_L)||_w
+ * (0 for one level). */
+mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean_l,
+                          double* var_l, double* V_l, int64_t* N_l, double* rmse, void* stream);
+
+/* Whole MLMC run with fixed sample counts (host N_l[n_levels]): for each level
+ * l, sample ids 0..N_l-1 in batches of at most `batch` pairs, mlmc_sample_level
+ * + mlmc_accumulate; then mlmc_estimate into the host outputs (as above;
+ * synchronises the stream).  ws: mlmc_run_workspace_bytes(ctx, batch) bytes.
+ * C_l (host [n_levels], may be NULL): device time per pair of each level, s.
+ * stats (host [8], may be NULL): device ms spent in the per-sample solve
+ * kernel (CUDA events around its launches), its launch count, CG and Newton
+ * iterations summed over samples and weighted by the nodes of their grid,
+ * CG truncations, line-search halvings, non-converged solves, and the total
+ * number of kernels launched.  Returns MLMC_ERR_NOT_CONVERGED (outputs still
+ * written) if any solve failed. */
+mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed, int batch, void* ws,
+                     size_t ws_bytes, double* mean, double* var, double* V_l, double* C_l,
+                     double* rmse, double* stats, void* stream);
+/* Workspace bytes for mlmc_run with the given batch. */
+mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, int batch, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLMC_H */

@@ -1,0 +1,290 @@
+"""Thin Python binding of the C ABI in ``include/mlmc.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``lib/libmlmc_gb300.so``.  Device memory and streams come from
+PyTorch (tensors' ``data_ptr()`` and ``torch.cuda.current_stream()``).  If the
+library is missing the import of this module still works, but every call
+raises -- there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libmlmc_gb300.so")
+
+MLMC_MAX_LEVELS = 8
+MLMC_OK = 0
+MLMC_PREC_FP64 = 0
+MLMC_PREC_MIXED = 1
+STATUS = {0: "MLMC_OK", -1: "MLMC_ERR_ARG", -2: "MLMC_ERR_OOM", -3: "MLMC_ERR_NOT_CONVERGED",
+          -4: "MLMC_ERR_TIMEOUT", -5: "MLMC_ERR_CUDA", -6: "MLMC_ERR_WORKSPACE"}
+
+
+class mlmc_config(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_levels", C.c_int), ("n0", C.c_int * 3), ("m0", C.c_int),
+                ("L", C.c_double * 3), ("T", C.c_double), ("c", C.c_double), ("a", C.c_double),
+                ("s_t", C.c_double), ("s_l0", C.c_double), ("theta0_deg", C.c_double),
+                ("theta1_deg", C.c_double), ("stim_r", C.c_double), ("stim_c", C.c_double * 3),
+                ("kl_sigma2", C.c_double), ("kl_ell", C.c_double), ("kl_modes", C.c_int),
+                ("precision", C.c_int), ("newton_tol", C.c_double), ("newton_max", C.c_int),
+                ("lin_rtol", C.c_double), ("lin_max", C.c_int)]
+
+
+class mlmc_sample_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("failed_step", C.c_int32), ("newton_iters", C.c_int32),
+                ("cg_iters", C.c_int32), ("truncations", C.c_int32), ("halvings", C.c_int32),
+                ("max_newton", C.c_int32), ("pad", C.c_int32)]
+
+
+INFO_FIELDS = [f[0] for f in mlmc_sample_info._fields_ if f[0] != "pad"]
+
+_lib = None
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing; run __graft_entry__.build() "
+                               "(there is no CPU fallback)" % LIB_PATH)
+        l = C.CDLL(LIB_PATH)
+        vp, i64, i32, u64, sz = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64, C.c_size_t
+        ip = C.c_int
+        sig = {
+            "mlmc_create": ([C.POINTER(mlmc_config), C.POINTER(vp)], ip),
+            "mlmc_destroy": ([vp], None),
+            "mlmc_last_error": ([vp], C.c_char_p),
+            "mlmc_level_info": ([vp, ip, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)], ip),
+            "mlmc_workspace_bytes": ([vp, ip, ip, C.POINTER(sz)], ip),
+            "mlmc_xi": ([vp, u64, ip, vp, ip, vp, vp], ip),
+            "mlmc_kl_field": ([vp, ip, vp, ip, vp, vp], ip),
+            "mlmc_solve": ([vp, ip, vp, ip, vp, vp, vp, vp, sz, vp], ip),
+            "mlmc_slab_residual": ([vp, ip, vp, vp, ip, vp, vp, vp], ip),
+            "mlmc_activation": ([vp, ip, vp, ip, vp, vp], ip),
+            "mlmc_sample_level": ([vp, ip, u64, vp, ip, vp, vp, vp, vp, vp, vp, sz, vp], ip),
+            "mlmc_accumulate": ([vp, ip, vp, vp, ip, vp], ip),
+            "mlmc_reset": ([vp, vp], ip),
+            "mlmc_estimate": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], ip),
+            "mlmc_run": ([vp, vp, u64, ip, vp, sz, vp, vp, vp, vp, vp, vp, vp], ip),
+            "mlmc_run_workspace_bytes": ([vp, ip, C.POINTER(sz)], ip),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = l
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C-ABI functions this binding declares."""
+    return ["mlmc_create", "mlmc_destroy", "mlmc_last_error", "mlmc_level_info",
+            "mlmc_workspace_bytes", "mlmc_xi", "mlmc_kl_field", "mlmc_solve", "mlmc_slab_residual",
+            "mlmc_activation", "mlmc_sample_level", "mlmc_accumulate", "mlmc_reset",
+            "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes"]
+
+
+def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=200, lin_rtol=1e-12,
+                lin_max=5000, levels=None):
+    """mlmc_config from a workload dictionary (see workloads.py)."""
+    c = mlmc_config()
+    c.dim = w["dim"]
+    c.n_levels = levels if levels is not None else w["levels"]
+    for d in range(3):
+        c.n0[d] = int(w["n0"][d]) if d < len(w["n0"]) else 1
+        c.L[d] = float(w["L"][d]) if d < len(w["L"]) else 1.0
+        c.stim_c[d] = float(w["stim_c"][d]) if d < len(w["stim_c"]) else 0.0
+    c.m0 = w["m0"]
+    c.T, c.c, c.a = w["T"], w["c"], w["a"]
+    c.s_t, c.s_l0 = w["s_t"], w["s_l0"]
+    c.theta0_deg, c.theta1_deg = w["theta0"], w["theta1"]
+    c.stim_r = w["stim_r"]
+    c.kl_sigma2, c.kl_ell, c.kl_modes = w["sigma2"], w["ell"], w["M"]
+    c.precision = precision
+    c.newton_tol, c.newton_max, c.lin_rtol, c.lin_max = newton_tol, newton_max, lin_rtol, lin_max
+    return c
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One ``mlmc_ctx`` plus torch-allocated outputs and workspaces."""
+
+    def __init__(self, cfg):
+        self.cfg = cfg
+        h = C.c_void_p()
+        st = lib().mlmc_create(C.byref(cfg), C.byref(h))
+        if st != MLMC_OK:
+            raise MLMCError(st, lib().mlmc_last_error(None).decode())
+        self.h = h
+        self._ws = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mlmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != MLMC_OK:
+            raise MLMCError(st, lib().mlmc_last_error(self.h).decode())
+
+    # ---------------------------------------------------------------- sizes
+    def level_info(self, level):
+        n, c, m = C.c_int64(), C.c_int64(), C.c_int32()
+        self._check(lib().mlmc_level_info(self.h, level, C.byref(n), C.byref(c), C.byref(m)))
+        return n.value, c.value, m.value
+
+    def workspace_bytes(self, level, n):
+        b = C.c_size_t()
+        self._check(lib().mlmc_workspace_bytes(self.h, level, n, C.byref(b)))
+        return b.value
+
+    def run_workspace_bytes(self, batch):
+        b = C.c_size_t()
+        self._check(lib().mlmc_run_workspace_bytes(self.h, batch, C.byref(b)))
+        return b.value
+
+    def workspace(self, nbytes, key="ws"):
+        import torch
+        w = self._ws.get(key)
+        if w is None or w.numel() < nbytes:
+            w = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+            self._ws[key] = w
+        return w
+
+    # ---------------------------------------------------------------- steps
+    def xi(self, seed, level, ids, stream=None):
+        import torch
+        ids = ids.to(device="cuda", dtype=torch.int64).contiguous()
+        out = torch.empty((ids.numel(), self.cfg.kl_modes), dtype=torch.float64, device="cuda")
+        self._check(lib().mlmc_xi(self.h, seed, level, _p(ids), ids.numel(), _p(out), _stream(stream)))
+        return out
+
+    def kl_field(self, level, xi, stream=None):
+        import torch
+        _, cells, _ = self.level_info(level)
+        xi = xi.contiguous()
+        out = torch.empty((xi.shape[0], cells), dtype=torch.float64, device="cuda")
+        self._check(lib().mlmc_kl_field(self.h, level, _p(xi), xi.shape[0], _p(out), _stream(stream)))
+        return out
+
+    def solve(self, level, Z, slab=False, stream=None):
+        import torch
+        nodes, _, m = self.level_info(level)
+        n = Z.shape[0]
+        Z = Z.contiguous()
+        t = torch.empty((n, nodes), dtype=torch.float64, device="cuda")
+        sl = torch.empty((n, m + 1, nodes), dtype=torch.float64, device="cuda") if slab else None
+        info = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
+        nb = self.workspace_bytes(level, n)
+        ws = self.workspace(nb)
+        self._check(lib().mlmc_solve(self.h, level, _p(Z), n, _p(t), _p(sl), _p(info), _p(ws),
+                                     ws.numel(), _stream(stream)))
+        return t, sl, info
+
+    def slab_residual(self, level, Z, slab, full=True, stream=None):
+        import torch
+        n = slab.shape[0]
+        nodes, _, m = self.level_info(level)
+        F = torch.empty((n, m, nodes), dtype=torch.float64, device="cuda") if full else None
+        rmax = torch.empty(n, dtype=torch.float64, device="cuda")
+        self._check(lib().mlmc_slab_residual(self.h, level, _p(Z.contiguous()), _p(slab.contiguous()),
+                                             n, _p(F), _p(rmax), _stream(stream)))
+        return F, rmax
+
+    def activation(self, level, slab, stream=None):
+        import torch
+        n = slab.shape[0]
+        nodes, _, _ = self.level_info(level)
+        t = torch.empty((n, nodes), dtype=torch.float64, device="cuda")
+        self._check(lib().mlmc_activation(self.h, level, _p(slab.contiguous()), n, _p(t), _stream(stream)))
+        return t
+
+    def sample_level(self, level, seed, ids, want_maps=False, stream=None):
+        import torch
+        ids = ids.to(device="cuda", dtype=torch.int64).contiguous()
+        n = ids.numel()
+        n0, _, _ = self.level_info(0)
+        y = torch.empty((n, n0), dtype=torch.float64, device="cuda")
+        y2 = torch.empty_like(y)
+        tf = tc = None
+        if want_maps:
+            tf = torch.empty((n, self.level_info(level)[0]), dtype=torch.float64, device="cuda")
+            if level > 0:
+                tc = torch.empty((n, self.level_info(level - 1)[0]), dtype=torch.float64, device="cuda")
+        info = torch.zeros((2 * n, 8), dtype=torch.int32, device="cuda")
+        nb = self.workspace_bytes(level, n)
+        ws = self.workspace(nb)
+        self._check(lib().mlmc_sample_level(self.h, level, seed, _p(ids), n, _p(y), _p(y2), _p(tf),
+                                            _p(tc), _p(info), _p(ws), ws.numel(), _stream(stream)))
+        return y, y2, tf, tc, info
+
+    def accumulate(self, level, y, y2, stream=None):
+        self._check(lib().mlmc_accumulate(self.h, level, _p(y.contiguous()), _p(y2.contiguous()),
+                                          y.shape[0], _stream(stream)))
+
+    def reset(self, stream=None):
+        self._check(lib().mlmc_reset(self.h, _stream(stream)))
+
+    def estimate(self, stream=None):
+        L = self.cfg.n_levels
+        n0, _, _ = self.level_info(0)
+        mean, var = np.zeros(n0), np.zeros(n0)
+        mean_l, var_l = np.zeros((L, n0)), np.zeros((L, n0))
+        V = np.zeros(L)
+        N = np.zeros(L, np.int64)
+        rmse = C.c_double()
+        dp = lambda a: a.ctypes.data_as(C.c_void_p)
+        self._check(lib().mlmc_estimate(self.h, dp(mean), dp(var), dp(mean_l), dp(var_l), dp(V),
+                                        dp(N), C.byref(rmse), _stream(stream)))
+        return dict(mean=mean, var=var, mean_l=mean_l, var_l=var_l, V_l=V, N_l=N, rmse=rmse.value)
+
+    def run(self, N_l, seed=0, batch=None, stream=None):
+        """Whole MLMC run with fixed counts; host outputs (the end-to-end call).
+        ``stats``: solve-kernel device ms, solve launches, CG and Newton
+        node-iterations, truncations, halvings, failed solves, kernel launches."""
+        L = self.cfg.n_levels
+        batch = batch or int(max(N_l))
+        n0, _, _ = self.level_info(0)
+        Nh = np.ascontiguousarray(N_l, np.int64)
+        mean, var, V, Cl = np.zeros(n0), np.zeros(n0), np.zeros(L), np.zeros(L)
+        stats = np.zeros(8)
+        rmse = C.c_double()
+        nb = self.run_workspace_bytes(batch)
+        ws = self.workspace(nb, key="run")
+        dp = lambda a: a.ctypes.data_as(C.c_void_p)
+        self._check(lib().mlmc_run(self.h, dp(Nh), seed, batch, _p(ws), ws.numel(), dp(mean), dp(var),
+                                   dp(V), dp(Cl), C.byref(rmse), dp(stats), _stream(stream)))
+        keys = ("solve_ms", "solve_launches", "cg_node_iters", "newton_node_iters", "truncations",
+                "halvings", "failed", "launches")
+        return dict(mean=mean, var=var, V_l=V, C_l=Cl, rmse=rmse.value, N_l=Nh,
+                    stats=dict(zip(keys, stats.tolist())))
+
+
+def info_dicts(info):
+    """Per-sample solver reports from an info tensor [n][8]."""
+    a = info.cpu().numpy()
+    return [dict(zip(INFO_FIELDS, row[:7].tolist())) for row in a]

@@ -1,0 +1,534 @@
+// The C ABI (include/mlmc.h): argument checking, workspace carving, and the
+// host-side orchestration of the per-level pipeline.  No arithmetic of the
+// method runs here except the KL mode table (built once per context).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mlmc {
+void kl_1d_host(double len, double ell, int n, std::vector<double>& omega, std::vector<double>& lam,
+                std::vector<double>& nrm);
+bool kl_table_host(int dim, const double* L, double sigma2, double ell, int M, std::vector<int>& idx,
+                   std::vector<double>& sqrt_lam);
+void kl_phi_table_host(double len, double ell, int n1d, int n_axis, std::vector<double>& out);
+cudaError_t launch_iota(uint64_t first, int n, uint64_t* ids, cudaStream_t st);
+}  // namespace mlmc
+
+using namespace mlmc;
+
+struct mlmc_ctx {
+  mlmc_config cfg;
+  int device;
+  LevelDesc lv[MLMC_MAX_LEVELS];
+  Physics ph;
+  SolverParams sp;
+  int M;
+  double* d_sqrt_lam = nullptr;
+  int* d_idx = nullptr;
+  double* d_phi[MLMC_MAX_LEVELS][3] = {};
+  double* d_acc = nullptr;        // [3][levels][nodes0]: mean, M2, mean of Y2
+  int64_t* d_N = nullptr;         // [levels]
+  double* d_est = nullptr;        // estimate output
+  unsigned long long* d_cnt = nullptr;  // solver counters (see N_COUNTERS)
+  int64_t N_acc[MLMC_MAX_LEVELS] = {};
+  // launch accounting and solve-kernel timing, active inside mlmc_run
+  bool prof = false;
+  long launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+static mlmc_status fail(mlmc_ctx* ctx, mlmc_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg; else g_create_error = msg;
+  return st;
+}
+
+static mlmc_status cuda_fail(mlmc_ctx* ctx, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA, m);
+}
+
+#define CK(ctx, expr)                                        \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr); \
+  } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// --------------------------------------------------------------- workspace
+struct SolveWs {
+  size_t coef64, coef32, ubuf, F, Ku, Kd, kr, total;
+};
+
+static SolveWs solve_ws(const LevelDesc& lv, int n, bool mixed) {
+  SolveWs w;
+  size_t N = (size_t)lv.nodes, NO = (size_t)n_offsets(lv.dim), kr = mixed ? 4 : 8;
+  size_t off = 0;
+  w.coef64 = off; off += align256((size_t)n * NO * N * 8);
+  w.coef32 = off; off += mixed ? align256((size_t)n * NO * N * 4) : 0;
+  w.ubuf = off; off += align256((size_t)n * 2 * N * 8);
+  w.F = off; off += align256((size_t)n * N * 8);
+  w.Ku = off; off += align256((size_t)n * N * 8);
+  w.Kd = off; off += align256((size_t)n * N * 8);
+  w.kr = off; off += align256((size_t)n * 7 * N * kr);
+  w.total = off;
+  return w;
+}
+
+struct PairWs {
+  size_t xi, Zf, Zc, tf, tc, info, solve, total;
+};
+
+static PairWs pair_ws(const mlmc_ctx* c, int level, int n) {
+  PairWs w;
+  const LevelDesc& lf = c->lv[level];
+  size_t off = 0;
+  w.xi = off; off += align256((size_t)n * c->M * 8);
+  w.Zf = off; off += align256((size_t)n * lf.cells * 8);
+  w.Zc = off; off += level > 0 ? align256((size_t)n * c->lv[level - 1].cells * 8) : 0;
+  w.tf = off; off += align256((size_t)n * lf.nodes * 8);
+  w.tc = off; off += level > 0 ? align256((size_t)n * c->lv[level - 1].nodes * 8) : 0;
+  w.info = off; off += align256((size_t)2 * n * sizeof(mlmc_sample_info));
+  w.solve = off;
+  bool mixed = c->cfg.precision == MLMC_PREC_MIXED;
+  size_t s = solve_ws(lf, n, mixed).total;
+  if (level > 0) {
+    size_t sc = solve_ws(c->lv[level - 1], n, mixed).total;
+    s = s > sc ? s : sc;
+  }
+  off += s;
+  w.total = off;
+  return w;
+}
+
+static bool check_ws(mlmc_ctx* ctx, void* ws, size_t have, size_t need) {
+  if (!ws || have < need || ((uintptr_t)ws & 255)) {
+    char b[160];
+    snprintf(b, sizeof b, "workspace %p of %zu bytes: need %zu bytes, 256-byte aligned", ws, have,
+             need);
+    ctx->err = b;
+    return false;
+  }
+  return true;
+}
+
+// --------------------------------------------------------------- create
+extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
+  if (!out) return fail(nullptr, MLMC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, MLMC_ERR_ARG, "cfg is NULL");
+  const mlmc_config& c = *cfg;
+  if (c.dim != 2 && c.dim != 3) return fail(nullptr, MLMC_ERR_ARG, "dim must be 2 or 3");
+  if (c.n_levels < 1 || c.n_levels > MLMC_MAX_LEVELS)
+    return fail(nullptr, MLMC_ERR_ARG, "n_levels out of range");
+  for (int d = 0; d < c.dim; ++d)
+    if (c.n0[d] < 1 || !(c.L[d] > 0.0)) return fail(nullptr, MLMC_ERR_ARG, "n0 and L must be positive");
+  if (c.m0 < 1 || !(c.T > 0.0)) return fail(nullptr, MLMC_ERR_ARG, "m0 and T must be positive");
+  if (c.kl_modes < 1 || c.kl_modes > 4096 || !(c.kl_ell > 0.0) || !(c.kl_sigma2 >= 0.0))
+    return fail(nullptr, MLMC_ERR_ARG, "KL parameters out of range");
+  if (c.precision != MLMC_PREC_FP64 && c.precision != MLMC_PREC_MIXED)
+    return fail(nullptr, MLMC_ERR_ARG, "unknown precision");
+  if (!(c.newton_tol > 0.0) || c.newton_max < 1 || !(c.lin_rtol > 0.0) || c.lin_max < 1)
+    return fail(nullptr, MLMC_ERR_ARG, "solver tolerances / iteration caps must be positive");
+  if (!(c.s_t > 0.0) || !(c.s_l0 > 0.0)) return fail(nullptr, MLMC_ERR_ARG, "conductivities must be positive");
+
+  mlmc_ctx* ctx = new mlmc_ctx();
+  ctx->cfg = c;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e != cudaSuccess) { delete ctx; return fail(nullptr, MLMC_ERR_CUDA, cudaGetErrorString(e)); }
+  const double pi = 3.141592653589793238462643;
+  for (int l = 0; l < c.n_levels; ++l) {
+    LevelDesc& lv = ctx->lv[l];
+    lv.dim = c.dim;
+    int64_t nodes = 1, cells = 1;
+    double vol = 1.0;
+    for (int d = 0; d < 3; ++d) {
+      if (d < c.dim) {
+        int64_t nn = (int64_t)c.n0[d] << l;
+        if (nn > (1 << 20)) { delete ctx; return fail(nullptr, MLMC_ERR_ARG, "grid too large"); }
+        lv.n[d] = (int)nn; lv.N[d] = (int)nn + 1; lv.h[d] = c.L[d] / (double)nn;
+      } else {
+        lv.n[d] = 1; lv.N[d] = 1; lv.h[d] = 1.0;
+      }
+      nodes *= lv.N[d]; cells *= lv.n[d]; vol *= (d < c.dim ? lv.h[d] : 1.0);
+    }
+    if (nodes > (int64_t)1 << 31) { delete ctx; return fail(nullptr, MLMC_ERR_ARG, "grid too large"); }
+    lv.nodes = nodes; lv.cells = cells; lv.vol = vol;
+    lv.m = (int)((int64_t)c.m0 << l);
+    lv.T = c.T;
+    lv.dt = c.T / (double)lv.m;
+  }
+  Physics& ph = ctx->ph;
+  ph.c = c.c; ph.a = c.a; ph.s_t = c.s_t; ph.s_l0 = c.s_l0;
+  ph.th0 = c.theta0_deg * pi / 180.0;
+  ph.th1 = c.theta1_deg * pi / 180.0;
+  ph.Lz = c.dim == 3 ? c.L[2] : 1.0;
+  ph.stim_r2 = c.stim_r * c.stim_r;
+  for (int d = 0; d < 3; ++d) ph.stim_c[d] = c.stim_c[d];
+  SolverParams& sp = ctx->sp;
+  sp.newton_tol = c.newton_tol;
+  sp.newton_max = c.newton_max;
+  sp.lin_rtol = c.precision == MLMC_PREC_MIXED ? fmax(c.lin_rtol, 1e-5) : c.lin_rtol;
+  sp.lin_max = c.lin_max;
+  sp.ls_full_step = 1e-6;
+
+  // KL mode table and per-level 1D mode values at the cell centroids
+  ctx->M = c.kl_modes;
+  std::vector<int> idx;
+  std::vector<double> sl;
+  if (!kl_table_host(c.dim, c.L, c.kl_sigma2, c.kl_ell, c.kl_modes, idx, sl)) {
+    delete ctx;
+    return fail(nullptr, MLMC_ERR_ARG, "KL mode table could not be built");
+  }
+  int n1d[3] = {0, 0, 0};
+  for (int q = 0; q < c.kl_modes; ++q)
+    for (int d = 0; d < 3; ++d) n1d[d] = idx[3 * q + d] + 1 > n1d[d] ? idx[3 * q + d] + 1 : n1d[d];
+  auto cleanup_fail = [&](cudaError_t err, const char* where) {
+    mlmc_destroy(ctx);
+    return fail(nullptr, err == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(err));
+  };
+  if ((e = cudaMalloc(&ctx->d_sqrt_lam, sizeof(double) * c.kl_modes)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&ctx->d_idx, sizeof(int) * 3 * c.kl_modes)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+  if ((e = cudaMemcpy(ctx->d_sqrt_lam, sl.data(), sizeof(double) * c.kl_modes, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
+  if ((e = cudaMemcpy(ctx->d_idx, idx.data(), sizeof(int) * 3 * c.kl_modes, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
+  for (int l = 0; l < c.n_levels; ++l)
+    for (int d = 0; d < c.dim; ++d) {
+      std::vector<double> tab;
+      kl_phi_table_host(c.L[d], c.kl_ell, n1d[d], ctx->lv[l].n[d], tab);
+      if ((e = cudaMalloc(&ctx->d_phi[l][d], sizeof(double) * tab.size())) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+      if ((e = cudaMemcpy(ctx->d_phi[l][d], tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
+    }
+  int64_t n0 = ctx->lv[0].nodes;
+  int L = c.n_levels;
+  size_t est = (size_t)(2 * n0 + 2 * (int64_t)L * n0 + L + 2);
+  if ((e = cudaMalloc(&ctx->d_acc, sizeof(double) * 3 * L * n0)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&ctx->d_N, sizeof(int64_t) * L)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&ctx->d_est, sizeof(double) * est)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&ctx->d_cnt, sizeof(unsigned long long) * N_COUNTERS)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+  if ((e = cudaMemset(ctx->d_acc, 0, sizeof(double) * 3 * L * n0)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
+  if ((e = cudaMemset(ctx->d_cnt, 0, sizeof(unsigned long long) * N_COUNTERS)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
+  *out = ctx;
+  return MLMC_OK;
+}
+
+extern "C" void mlmc_destroy(mlmc_ctx* ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->d_sqrt_lam);
+  cudaFree(ctx->d_idx);
+  for (int l = 0; l < MLMC_MAX_LEVELS; ++l)
+    for (int d = 0; d < 3; ++d) cudaFree(ctx->d_phi[l][d]);
+  cudaFree(ctx->d_acc);
+  cudaFree(ctx->d_N);
+  cudaFree(ctx->d_est);
+  cudaFree(ctx->d_cnt);
+  for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+extern "C" const char* mlmc_last_error(const mlmc_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+static bool bad_level(mlmc_ctx* ctx, int level) {
+  if (level < 0 || level >= ctx->cfg.n_levels) {
+    ctx->err = "level out of range";
+    return true;
+  }
+  return false;
+}
+
+extern "C" mlmc_status mlmc_level_info(const mlmc_ctx* ctx, int level, int64_t* nodes,
+                                       int64_t* cells, int32_t* steps) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (level < 0 || level >= ctx->cfg.n_levels) return MLMC_ERR_ARG;
+  if (nodes) *nodes = ctx->lv[level].nodes;
+  if (cells) *cells = ctx->lv[level].cells;
+  if (steps) *steps = ctx->lv[level].m;
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_workspace_bytes(const mlmc_ctx* ctx, int level, int n, size_t* bytes) {
+  if (!ctx || !bytes || n < 0) return MLMC_ERR_ARG;
+  if (level < 0 || level >= ctx->cfg.n_levels) return MLMC_ERR_ARG;
+  *bytes = pair_ws(ctx, level, n).total;
+  return MLMC_OK;
+}
+
+// --------------------------------------------------------------- steps
+extern "C" mlmc_status mlmc_xi(mlmc_ctx* ctx, uint64_t seed, int level, const uint64_t* ids, int n,
+                               double* xi, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (n < 0 || (n > 0 && (!ids || !xi))) return fail(ctx, MLMC_ERR_ARG, "mlmc_xi: bad arguments");
+  if (level < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_xi: negative level");
+  CK(ctx, launch_xi(seed, level, ids, n, ctx->M, xi, (cudaStream_t)stream));
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
+                                     void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level)) return MLMC_ERR_ARG;
+  if (n < 0 || (n > 0 && (!xi || !Z))) return fail(ctx, MLMC_ERR_ARG, "mlmc_kl_field: bad arguments");
+  CK(ctx, launch_kl_field(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_idx, ctx->d_phi[level][0],
+                          ctx->d_phi[level][1], ctx->d_phi[level][2], 0, xi, n, Z,
+                          (cudaStream_t)stream));
+  ctx->launches += 1;
+  return MLMC_OK;
+}
+
+// Coefficients + sweep for n samples of one level inside an already checked
+// workspace region.
+static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, double* t_act,
+                              double* slab, mlmc_sample_info* info, char* ws, cudaStream_t st) {
+  const LevelDesc& lv = ctx->lv[level];
+  bool mixed = ctx->cfg.precision == MLMC_PREC_MIXED;
+  SolveWs w = solve_ws(lv, n, mixed);
+  double* coef64 = (double*)(ws + w.coef64);
+  float* coef32 = mixed ? (float*)(ws + w.coef32) : nullptr;
+  CK(ctx, launch_assemble(lv, ctx->ph, Z, n, coef64, coef32, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->prof) {
+    while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+      cudaEvent_t ev;
+      CK(ctx, cudaEventCreate(&ev));
+      ctx->ev_pool.push_back(ev);
+    }
+    e0 = ctx->ev_pool[ctx->ev_used++];
+    e1 = ctx->ev_pool[ctx->ev_used++];
+    CK(ctx, cudaEventRecord(e0, st));
+  }
+  CK(ctx, launch_solve(lv, ctx->ph, ctx->sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
+                       (double*)(ws + w.F), (double*)(ws + w.Ku), (double*)(ws + w.Kd),
+                       (void*)(ws + w.kr), t_act, info, ctx->d_cnt, st));
+  if (ctx->prof) CK(ctx, cudaEventRecord(e1, st));
+  ctx->launches += 2;
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_solve(mlmc_ctx* ctx, int level, const double* Z, int n, double* t_act,
+                                  double* slab, mlmc_sample_info* info, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level)) return MLMC_ERR_ARG;
+  if (n < 0 || n > 65535 || (n > 0 && (!Z || !t_act)))
+    return fail(ctx, MLMC_ERR_ARG, "mlmc_solve: bad arguments");
+  size_t need = solve_ws(ctx->lv[level], n, ctx->cfg.precision == MLMC_PREC_MIXED).total;
+  if (!check_ws(ctx, ws, ws_bytes, need)) return MLMC_ERR_WORKSPACE;
+  if (n == 0) return MLMC_OK;
+  return solve_into(ctx, level, Z, n, t_act, slab, info, (char*)ws, (cudaStream_t)stream);
+}
+
+extern "C" mlmc_status mlmc_slab_residual(mlmc_ctx* ctx, int level, const double* Z,
+                                          const double* slab, int n, double* F, double* res_max,
+                                          void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level)) return MLMC_ERR_ARG;
+  if (n < 0 || n > 65535 || (n > 0 && (!Z || !slab)))
+    return fail(ctx, MLMC_ERR_ARG, "mlmc_slab_residual: bad arguments");
+  if (n == 0) return MLMC_OK;
+  const LevelDesc& lv = ctx->lv[level];
+  // couplings are rebuilt into a context-independent scratch owned by this call
+  double* coef = nullptr;
+  size_t bytes = (size_t)n * n_offsets(lv.dim) * lv.nodes * 8;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(ctx, cudaMallocAsync((void**)&coef, bytes, st));
+  cudaError_t e = launch_assemble(lv, ctx->ph, Z, n, coef, nullptr, st);
+  if (e == cudaSuccess) e = launch_slab_residual(lv, ctx->ph, coef, slab, n, F, res_max, st);
+  cudaError_t e2 = cudaFreeAsync(coef, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlmc_slab_residual");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_activation(mlmc_ctx* ctx, int level, const double* slab, int n,
+                                       double* t_act, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level)) return MLMC_ERR_ARG;
+  if (n < 0 || (n > 0 && (!slab || !t_act))) return fail(ctx, MLMC_ERR_ARG, "mlmc_activation: bad arguments");
+  CK(ctx, launch_activation(ctx->lv[level], slab, n, t_act, (cudaStream_t)stream));
+  return MLMC_OK;
+}
+
+static mlmc_status sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* ids,
+                                     int n, double* y, double* y2, double* t_fine, double* t_coarse,
+                                     mlmc_sample_info* info, char* ws, cudaStream_t st) {
+  PairWs w = pair_ws(ctx, level, n);
+  double* xi = (double*)(ws + w.xi);
+  double* Zf = (double*)(ws + w.Zf);
+  double* tf = t_fine ? t_fine : (double*)(ws + w.tf);
+  mlmc_sample_info* inf = info ? info : (mlmc_sample_info*)(ws + w.info);
+  CK(ctx, launch_xi(seed, level, ids, n, ctx->M, xi, st));
+  ctx->launches += 1;
+  mlmc_status r;
+  if ((r = mlmc_kl_field(ctx, level, xi, n, Zf, st)) != MLMC_OK) return r;
+  if ((r = solve_into(ctx, level, Zf, n, tf, nullptr, inf, ws + w.solve, st)) != MLMC_OK) return r;
+  double* tc = nullptr;
+  if (level > 0) {
+    double* Zc = (double*)(ws + w.Zc);
+    tc = t_coarse ? t_coarse : (double*)(ws + w.tc);
+    if ((r = mlmc_kl_field(ctx, level - 1, xi, n, Zc, st)) != MLMC_OK) return r;
+    if ((r = solve_into(ctx, level - 1, Zc, n, tc, nullptr, inf + n, ws + w.solve, st)) != MLMC_OK) return r;
+  }
+  CK(ctx, launch_pair_diff(ctx->lv[0], ctx->lv[level], level > 0 ? &ctx->lv[level - 1] : nullptr, tf,
+                           tc, n, y, y2, st));
+  ctx->launches += 1;
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_sample_level(mlmc_ctx* ctx, int level, uint64_t seed,
+                                         const uint64_t* ids, int n, double* y, double* y2,
+                                         double* t_fine, double* t_coarse, mlmc_sample_info* info,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level)) return MLMC_ERR_ARG;
+  if (n < 0 || n > 65535 || (n > 0 && (!ids || !y || !y2)))
+    return fail(ctx, MLMC_ERR_ARG, "mlmc_sample_level: bad arguments");
+  if (!check_ws(ctx, ws, ws_bytes, pair_ws(ctx, level, n).total)) return MLMC_ERR_WORKSPACE;
+  if (n == 0) return MLMC_OK;
+  return sample_level_into(ctx, level, seed, ids, n, y, y2, t_fine, t_coarse, info, (char*)ws,
+                           (cudaStream_t)stream);
+}
+
+extern "C" mlmc_status mlmc_reset(mlmc_ctx* ctx, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(ctx, cudaMemsetAsync(ctx->d_acc, 0, sizeof(double) * 3 * ctx->cfg.n_levels * ctx->lv[0].nodes, st));
+  CK(ctx, cudaMemsetAsync(ctx->d_cnt, 0, sizeof(unsigned long long) * N_COUNTERS, st));
+  for (int l = 0; l < MLMC_MAX_LEVELS; ++l) ctx->N_acc[l] = 0;
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_accumulate(mlmc_ctx* ctx, int level, const double* y, const double* y2,
+                                       int n, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level)) return MLMC_ERR_ARG;
+  if (n < 0 || (n > 0 && (!y || !y2))) return fail(ctx, MLMC_ERR_ARG, "mlmc_accumulate: bad arguments");
+  int64_t n0 = ctx->lv[0].nodes, L = ctx->cfg.n_levels;
+  double* mean = ctx->d_acc + (int64_t)level * n0;
+  CK(ctx, launch_accumulate(n0, y, y2, n, ctx->N_acc[level], mean, mean + L * n0, mean + 2 * L * n0,
+                            (cudaStream_t)stream));
+  ctx->launches += 1;
+  ctx->N_acc[level] += n;
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean_l,
+                                     double* var_l, double* V_l, int64_t* N_l, double* rmse,
+                                     void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int L = ctx->cfg.n_levels;
+  int64_t n0 = ctx->lv[0].nodes;
+  std::vector<int64_t> Nh(ctx->N_acc, ctx->N_acc + L);
+  CK(ctx, cudaMemcpyAsync(ctx->d_N, Nh.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice, st));
+  CK(ctx, launch_estimate(L, n0, ctx->lv[0], ctx->d_N, ctx->d_acc, ctx->d_acc + (int64_t)L * n0,
+                          ctx->d_acc + 2 * (int64_t)L * n0, ctx->d_est, st));
+  ctx->launches += 1;
+  size_t est = (size_t)(2 * n0 + 2 * (int64_t)L * n0 + L + 2);
+  std::vector<double> h(est);
+  CK(ctx, cudaMemcpyAsync(h.data(), ctx->d_est, sizeof(double) * est, cudaMemcpyDeviceToHost, st));
+  CK(ctx, cudaStreamSynchronize(st));
+  const double* p = h.data();
+  if (mean) memcpy(mean, p, sizeof(double) * n0);
+  if (var) memcpy(var, p + n0, sizeof(double) * n0);
+  if (mean_l) memcpy(mean_l, p + 2 * n0, sizeof(double) * L * n0);
+  if (var_l) memcpy(var_l, p + 2 * n0 + (int64_t)L * n0, sizeof(double) * L * n0);
+  const double* Vp = p + 2 * n0 + 2 * (int64_t)L * n0;
+  if (V_l) memcpy(V_l, Vp, sizeof(double) * L);
+  if (N_l) memcpy(N_l, Nh.data(), sizeof(int64_t) * L);
+  if (rmse) *rmse = Vp[L + 1];
+  return MLMC_OK;
+}
+
+// --------------------------------------------------------------- whole run
+static size_t run_ws(const mlmc_ctx* c, int batch) {
+  size_t m = 0;
+  for (int l = 0; l < c->cfg.n_levels; ++l) {
+    size_t s = pair_ws(c, l, batch).total;
+    m = s > m ? s : m;
+  }
+  return align256((size_t)batch * 8) + 2 * align256((size_t)batch * c->lv[0].nodes * 8) + m;
+}
+
+extern "C" mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, int batch, size_t* bytes) {
+  if (!ctx || !bytes || batch < 1 || batch > 65535) return MLMC_ERR_ARG;
+  *bytes = run_ws(ctx, batch);
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed, int batch,
+                                void* ws, size_t ws_bytes, double* mean, double* var, double* V_l,
+                                double* C_l, double* rmse, double* stats, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (!N_l || batch < 1 || batch > 65535) return fail(ctx, MLMC_ERR_ARG, "mlmc_run: bad arguments");
+  int L = ctx->cfg.n_levels;
+  for (int l = 0; l < L; ++l)
+    if (N_l[l] < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_run: negative sample count");
+  if (!check_ws(ctx, ws, ws_bytes, run_ws(ctx, batch))) return MLMC_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = (char*)ws;
+  uint64_t* ids = (uint64_t*)p; p += align256((size_t)batch * 8);
+  double* y = (double*)p; p += align256((size_t)batch * ctx->lv[0].nodes * 8);
+  double* y2 = (double*)p; p += align256((size_t)batch * ctx->lv[0].nodes * 8);
+  mlmc_status r = mlmc_reset(ctx, stream);
+  if (r != MLMC_OK) return r;
+  ctx->prof = true;
+  ctx->ev_used = 0;
+  ctx->launches = 0;
+  struct ProfOff { mlmc_ctx* c; ~ProfOff() { c->prof = false; } } prof_off{ctx};
+  cudaEvent_t ev[MLMC_MAX_LEVELS + 1];
+  for (int l = 0; l <= L; ++l) CK(ctx, cudaEventCreate(&ev[l]));
+  for (int l = 0; l < L; ++l) {
+    CK(ctx, cudaEventRecord(ev[l], st));
+    for (int64_t first = 0; first < N_l[l]; first += batch) {
+      int nb = (int)((N_l[l] - first) < batch ? (N_l[l] - first) : batch);
+      CK(ctx, launch_iota((uint64_t)first, nb, ids, st));
+      ctx->launches += 1;
+      if ((r = sample_level_into(ctx, l, seed, ids, nb, y, y2, nullptr, nullptr, nullptr, p, st)) != MLMC_OK)
+        return r;
+      if ((r = mlmc_accumulate(ctx, l, y, y2, nb, stream)) != MLMC_OK) return r;
+    }
+  }
+  CK(ctx, cudaEventRecord(ev[L], st));
+  if ((r = mlmc_estimate(ctx, mean, var, nullptr, nullptr, V_l, nullptr, rmse, stream)) != MLMC_OK) return r;
+  for (int l = 0; l < L; ++l) {
+    float ms = 0.f;
+    CK(ctx, cudaEventElapsedTime(&ms, ev[l], ev[l + 1]));
+    if (C_l) C_l[l] = N_l[l] > 0 ? ms * 1e-3 / (double)N_l[l] : 0.0;
+  }
+  for (int l = 0; l <= L; ++l) cudaEventDestroy(ev[l]);
+  unsigned long long cnt[N_COUNTERS];
+  CK(ctx, cudaMemcpy(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
+  if (stats) {
+    double solve_ms = 0.0;
+    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+      float ms = 0.f;
+      CK(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+      solve_ms += ms;
+    }
+    stats[0] = solve_ms;
+    stats[1] = (double)(ctx->ev_used / 2);
+    stats[2] = (double)cnt[1];
+    stats[3] = (double)cnt[2];
+    stats[4] = (double)cnt[3];
+    stats[5] = (double)cnt[4];
+    stats[6] = (double)cnt[0];
+    stats[7] = (double)ctx->launches;
+  }
+  if (cnt[0]) {
+    char b[96];
+    snprintf(b, sizeof b, "mlmc_run: %llu sample solves did not converge", cnt[0]);
+    return fail(ctx, MLMC_ERR_NOT_CONVERGED, b);
+  }
+  return MLMC_OK;
+}

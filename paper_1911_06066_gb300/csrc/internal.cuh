@@ -1,0 +1,103 @@
+// Internal definitions shared by the CUDA translation units of the library.
+// Everything here is device-side layout and launch plumbing; the arithmetic of
+// each step lives in its own file (rng.cu, kl.cu, assemble.cu, solver.cu,
+// slab.cu, estimators.cu) and the C ABI in abi.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "mlmc.h"
+
+namespace mlmc {
+
+// Geometry of one grid level (Q1 nodes on a box, x fastest).
+struct LevelDesc {
+  int dim;
+  int n[3];        // cells per axis (1 on unused axes)
+  int N[3];        // nodes per axis (1 on unused axes)
+  int m;           // implicit-Euler steps
+  int64_t nodes, cells;
+  double h[3];     // cell sides (1 on unused axes)
+  double vol;      // cell volume (area in 2D)
+  double dt, T;
+};
+
+// Physical parameters copied by value into kernels.
+struct Physics {
+  double c, a, s_t, s_l0;
+  double th0, th1;       // fiber angle (radians) at z = 0 and z = L[2]
+  double Lz;
+  double stim_r2;        // squared stimulus radius
+  double stim_c[3];
+};
+
+struct SolverParams {
+  double newton_tol;
+  int newton_max;
+  double lin_rtol;
+  int lin_max;
+  double ls_full_step;   // max|d| below which the full Newton step is taken
+};
+
+// Number of stencil couplings per node (3^dim) and the centre index.
+__host__ __device__ inline int n_offsets(int dim) { return dim == 3 ? 27 : 9; }
+__host__ __device__ inline int centre_offset(int dim) { return dim == 3 ? 13 : 4; }
+
+// Lumped Q1 mass of node (i,j,k): cell volume times 1/2 per axis on which the
+// node lies on the boundary (the row sum of the consistent mass).
+__device__ inline double lumped_mass(const LevelDesc& lv, int i, int j, int k) {
+  double m = lv.vol;
+  if (i == 0 || i == lv.n[0]) m *= 0.5;
+  if (j == 0 || j == lv.n[1]) m *= 0.5;
+  if (lv.dim == 3 && (k == 0 || k == lv.n[2])) m *= 0.5;
+  return m;
+}
+
+__device__ inline void node_ijk(const LevelDesc& lv, int64_t A, int& i, int& j, int& k) {
+  i = (int)(A % lv.N[0]);
+  int64_t r = A / lv.N[0];
+  j = (int)(r % lv.N[1]);
+  k = (int)(r / lv.N[1]);
+}
+
+// Reaction r(u) = c u (1-u)(u-a) and its derivative.
+__device__ inline double rxn(const Physics& p, double u) { return p.c * u * (1.0 - u) * (u - p.a); }
+__device__ inline double rxn_d(const Physics& p, double u) {
+  return p.c * (-3.0 * u * u + 2.0 * (1.0 + p.a) * u - p.a);
+}
+
+// Kernels and launchers (defined in the .cu files).
+cudaError_t launch_xi(uint64_t seed, int level, const uint64_t* ids, int n, int M, double* xi,
+                      cudaStream_t st);
+cudaError_t launch_kl_field(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
+                            const double* phi_x, const double* phi_y, const double* phi_z,
+                            int n1d, const double* xi, int n, double* Z, cudaStream_t st);
+cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,
+                            double* coef64, float* coef32, cudaStream_t st);
+cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
+                         bool mixed, int n, const double* coef64, const float* coef32,
+                         double* slab, double* ubuf, double* F, double* Ku, double* Kd,
+                         void* kr, double* t_act, mlmc_sample_info* info,
+                         unsigned long long* counters, cudaStream_t st);
+// counters (device, may be NULL): [0] non-converged solves, [1] CG iterations x
+// nodes, [2] Newton iterations x nodes, [3] CG truncations, [4] halvings.
+constexpr int N_COUNTERS = 5;
+cudaError_t launch_slab_residual(const LevelDesc& lv, const Physics& ph, const double* coef64,
+                                 const double* slab, int n, double* F, double* res_max,
+                                 cudaStream_t st);
+cudaError_t launch_activation(const LevelDesc& lv, const double* slab, int n, double* t_act,
+                              cudaStream_t st);
+cudaError_t launch_pair_diff(const LevelDesc& l0, const LevelDesc& lf, const LevelDesc* lc,
+                             const double* tf, const double* tc, int n, double* y, double* y2,
+                             cudaStream_t st);
+cudaError_t launch_accumulate(int64_t nodes0, const double* y, const double* y2, int n,
+                              int64_t n_old, double* mean, double* m2, double* mean2,
+                              cudaStream_t st);
+cudaError_t launch_estimate(int levels, int64_t nodes0, const LevelDesc& l0, const int64_t* N_l,
+                            const double* mean_l, const double* m2_l, const double* mean2_l,
+                            double* out, cudaStream_t st);
+
+}  // namespace mlmc

@@ -1,0 +1,121 @@
+// Row a1: the KL random inputs xi (Sec. 2.2, Eq. KL-expansion-deterministic;
+// here xi_k ~ N(0,1)), drawn from a counter-based stream so that any sample of
+// any level can be generated independently and reproduced bit for bit.
+//
+// Philox4x32-10 follows its published definition (Salmon, Moraes, Dror, Shaw,
+// SC'11): ten rounds of two 32x32->64-bit multiplies (M0 = 0xD2511F53,
+// M1 = 0xCD9E8D57) with the Weyl key bumps (0x9E3779B9, 0xBB67AE85).
+//
+// Normal transform: Box-Muller.  ln and sin/cos are evaluated here from their
+// atanh / Maclaurin series with explicitly rounded intrinsics (__dmul_rn,
+// __dadd_rn, __ddiv_rn, __dsqrt_rn), never contracted into FMAs, so every
+// value is fixed by IEEE-754 round-to-nearest and matches any other
+// implementation of the same operation sequence.
+//
+// Counter of mode pair j of sample id s on level pair l under seed K:
+//   ctr = (j, lo32(s), hi32(s), l),  key = (lo32(K), hi32(K)).
+// The four output words give k1 = (w0 >> 5) 2^26 + (w1 >> 6) and
+// k2 = (w2 >> 5) 2^26 + (w3 >> 6); u1 = (k1 + 1) 2^-53 in (0,1],
+// u2 = k2 2^-53 in [0,1); xi_2j = r cos(2 pi u2), xi_2j+1 = r sin(2 pi u2),
+// r = sqrt(-2 ln u1).
+#include "internal.cuh"
+
+namespace mlmc {
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += W0; k1 += W1; }
+    uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+    uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// ln x for normal x in (0, 1]: x = f 2^e, f folded into [1/sqrt2, sqrt2),
+// ln f = 2 atanh(s), s = (f-1)/(f+1), series to s^25 (|s| <= 0.1716).
+__device__ double ln_series(double x) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((bits >> 52) & 0x7ffull) - 1022;
+  double f = __longlong_as_double((long long)((bits & ~(0x7ffull << 52)) | (1022ull << 52)));
+  if (f < 0.70710678118654752440) { f = __dmul_rn(f, 2.0); e = e - 1; }
+  double s = __ddiv_rn(__dsub_rn(f, 1.0), __dadd_rn(f, 1.0));
+  double s2 = __dmul_rn(s, s);
+  double p = __ddiv_rn(1.0, 25.0);
+  for (int j = 11; j >= 0; --j) p = __dadd_rn(__dmul_rn(p, s2), __ddiv_rn(1.0, (double)(2 * j + 1)));
+  double lnf = __dmul_rn(__dmul_rn(2.0, s), p);
+  return __dadd_rn(__dmul_rn((double)e, 0.69314718055994530942), lnf);
+}
+
+// sin and cos of 2 pi u, u in [0,1): exact quadrant split of 4u, reflection
+// onto [0, pi/4], Maclaurin series through phi^21 (sin) and phi^20 (cos).
+__device__ void sincos_2pi_series(double u, double* s_out, double* c_out) {
+  double t = __dmul_rn(4.0, u);
+  int q = (int)t;
+  double w = __dsub_rn(t, (double)q);
+  bool swap = false;
+  if (w > 0.5) { w = __dsub_rn(1.0, w); swap = true; }
+  double phi = __dmul_rn(w, 1.57079632679489661923);
+  double p2 = __dmul_rn(phi, phi);
+  double fs[11], fc[11];
+  double fact = 1.0;
+  for (int k = 0; k <= 21; ++k) {
+    if (k > 0) fact = __dmul_rn(fact, (double)k);
+    double coef = __ddiv_rn(1.0, fact);
+    int j = k / 2;
+    double sg = (j % 2) ? -1.0 : 1.0;
+    if (k % 2) fs[j] = __dmul_rn(sg, coef); else fc[j] = __dmul_rn(sg, coef);
+  }
+  double ps = fs[10], pc = fc[10];
+  for (int j = 9; j >= 0; --j) {
+    ps = __dadd_rn(__dmul_rn(ps, p2), fs[j]);
+    pc = __dadd_rn(__dmul_rn(pc, p2), fc[j]);
+  }
+  double sp = __dmul_rn(phi, ps), cp = pc;
+  double sq = swap ? cp : sp, cq = swap ? sp : cp;
+  switch (q & 3) {
+    case 0: *s_out = sq; *c_out = cq; break;
+    case 1: *s_out = cq; *c_out = -sq; break;
+    case 2: *s_out = -sq; *c_out = -cq; break;
+    default: *s_out = -cq; *c_out = sq; break;
+  }
+}
+
+// One thread per (sample, mode pair).
+__global__ void xi_kernel(uint64_t seed, int level, const uint64_t* __restrict__ ids, int n, int M,
+                          double* __restrict__ xi) {
+  int pairs = (M + 1) / 2;
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)n * pairs) return;
+  int s = (int)(g / pairs), j = (int)(g % pairs);
+  uint64_t id = ids[s];
+  uint32_t w[4];
+  philox4x32_10((uint32_t)j, (uint32_t)id, (uint32_t)(id >> 32), (uint32_t)level, (uint32_t)seed,
+                (uint32_t)(seed >> 32), w);
+  const double two_m53 = 1.1102230246251565404e-16;  // 2^-53, exact
+  unsigned long long k1 = ((unsigned long long)(w[0] >> 5) << 26) | (unsigned long long)(w[1] >> 6);
+  unsigned long long k2 = ((unsigned long long)(w[2] >> 5) << 26) | (unsigned long long)(w[3] >> 6);
+  double u1 = __dmul_rn(__ull2double_rn(k1 + 1ull), two_m53);
+  double u2 = __dmul_rn(__ull2double_rn(k2), two_m53);
+  double r = __dsqrt_rn(__dmul_rn(-2.0, ln_series(u1)));
+  double sn, cs;
+  sincos_2pi_series(u2, &sn, &cs);
+  xi[(int64_t)s * M + 2 * j] = __dmul_rn(r, cs);
+  if (2 * j + 1 < M) xi[(int64_t)s * M + 2 * j + 1] = __dmul_rn(r, sn);
+}
+
+cudaError_t launch_xi(uint64_t seed, int level, const uint64_t* ids, int n, int M, double* xi,
+                      cudaStream_t st) {
+  int64_t total = (int64_t)n * ((M + 1) / 2);
+  if (total == 0) return cudaSuccess;
+  int bs = 128;
+  xi_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(seed, level, ids, n, M, xi);
+  return cudaGetLastError();
+}
+
+}  // namespace mlmc
