@@ -198,6 +198,31 @@ mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed, int batch
 /* Workspace bytes for mlmc_run with the given batch. */
 mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, int batch, size_t* bytes);
 
+/* Allocation-free variant of mlmc_solve (the paper has no counterpart; this is
+ * a deployment aid).  For callers that may not allocate device memory -- for
+ * example code running under a host framework that reserved the whole device
+ * budget up front, a plugin that must not touch the device heap, or a caller
+ * that cannot afford the device-wide synchronisation an allocation may cause.
+ * The caller passes only inputs and outputs, exactly as for mlmc_solve
+ * (without the slab output): Z device [n][cells_l], t_act device [n][nodes_l],
+ * info device [n] or NULL, plus the configuration itself (no context needed).
+ *
+ * Scratch: one file-scope device array of MLMC_NOALLOC_SCRATCH_BYTES bytes,
+ * reserved on every device that loads the library and held until the process
+ * exits.  The call allocates nothing (no cudaMalloc/cudaFree, no allocating
+ * library routine).  Requests whose scratch would exceed the array are
+ * rejected with MLMC_ERR_WORKSPACE and a message naming both sizes (read it
+ * with mlmc_last_error(NULL)); other failures set the same message.
+ * The first call on a device looks up the array's device address (once per
+ * device, under a lock); make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind;
+ * the solve writes every scratch word before reading it, so nothing needs
+ * clearing, but calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on the scratch and must be serialised by the caller. */
+#define MLMC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int level, const double* Z, int n,
+                               double* t_act, mlmc_sample_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ def lib():
             "mlmc_estimate": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], ip),
             "mlmc_run": ([vp, vp, u64, ip, vp, sz, vp, vp, vp, vp, vp, vp, vp], ip),
             "mlmc_run_workspace_bytes": ([vp, ip, C.POINTER(sz)], ip),
+            "mlmc_solve_noalloc": ([C.POINTER(mlmc_config), ip, vp, ip, vp, vp, vp], ip),
         }
         for name, (args, res) in sig.items():
             f = getattr(l, name)
@@ -90,7 +91,7 @@ def exported_symbols():
     return ["mlmc_create", "mlmc_destroy", "mlmc_last_error", "mlmc_level_info",
             "mlmc_workspace_bytes", "mlmc_xi", "mlmc_kl_field", "mlmc_solve", "mlmc_slab_residual",
             "mlmc_activation", "mlmc_sample_level", "mlmc_accumulate", "mlmc_reset",
-            "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes"]
+            "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_solve_noalloc"]
 
 
 def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=200, lin_rtol=1e-12,

@@ -46,6 +46,11 @@ struct mlmc_ctx {
 
 static thread_local std::string g_create_error;
 
+namespace mlmc {
+// Message for mlmc_last_error(NULL) from entry points that take no context.
+void set_create_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace mlmc
+
 static mlmc_status fail(mlmc_ctx* ctx, mlmc_status st, const std::string& msg) {
   if (ctx) ctx->err = msg; else g_create_error = msg;
   return st;
