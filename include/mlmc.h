@@ -50,7 +50,8 @@ typedef enum {
 
 typedef enum {
   MLMC_PREC_FP64 = 0,   /* every step in FP64                                       */
-  MLMC_PREC_MIXED = 1   /* FP32 Krylov inner solves; FP64 residual, update, QoI     */
+  MLMC_PREC_MIXED = 1   /* FP32 Krylov inner solves on levels with c dt max r' <= 2
+                           (FP64 on the others); FP64 residual, update, QoI      */
 } mlmc_precision;
 
 /* Problem and solver configuration (plain data, copied by mlmc_create). */
@@ -75,7 +76,14 @@ typedef struct {
   int newton_max;        /* Newton iterations per time step                          */
   double lin_rtol;       /* CG relative tolerance (FP64 inner solves)                */
   int lin_max;           /* CG iterations per Newton step                            */
+  int solver;            /* mlmc_solver: kernel layout of the per-sample sweep        */
 } mlmc_config;
+
+typedef enum {
+  MLMC_SOLVER_AUTO = 0,    /* cluster layout where a sample fits, else block layout      */
+  MLMC_SOLVER_BLOCK = 1,   /* one thread block per sample, vectors in global memory      */
+  MLMC_SOLVER_CLUSTER = 2  /* one thread-block cluster per sample, vectors in shared memory */
+} mlmc_solver;
 
 /* Per-sample solver report, written by the solve calls (device array). */
 typedef struct {

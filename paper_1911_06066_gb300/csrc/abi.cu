@@ -70,6 +70,16 @@ static mlmc_status cuda_fail(mlmc_ctx* ctx, cudaError_t e, const char* where) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // --------------------------------------------------------------- workspace
+// FP32 inner solves are used only where the step Jacobian is at most mildly
+// indefinite: c dt max r' <= 2, max r' = c((1+a)^2/3 - a).  On more strongly
+// indefinite levels the negative-curvature decisions of an FP32 CG can pick a
+// different root than FP64 (observed on the 32^2 / dt = 5/64 level).
+static bool level_mixed(const mlmc_config& c, const LevelDesc& lv) {
+  if (c.precision != MLMC_PREC_MIXED) return false;
+  double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
+  return lv.dt * rmax <= 2.0;
+}
+
 struct SolveWs {
   size_t coef64, coef32, ubuf, F, Ku, Kd, kr, total;
 };
@@ -104,10 +114,9 @@ static PairWs pair_ws(const mlmc_ctx* c, int level, int n) {
   w.tc = off; off += level > 0 ? align256((size_t)n * c->lv[level - 1].nodes * 8) : 0;
   w.info = off; off += align256((size_t)2 * n * sizeof(mlmc_sample_info));
   w.solve = off;
-  bool mixed = c->cfg.precision == MLMC_PREC_MIXED;
-  size_t s = solve_ws(lf, n, mixed).total;
+  size_t s = solve_ws(lf, n, level_mixed(c->cfg, lf)).total;
   if (level > 0) {
-    size_t sc = solve_ws(c->lv[level - 1], n, mixed).total;
+    size_t sc = solve_ws(c->lv[level - 1], n, level_mixed(c->cfg, c->lv[level - 1])).total;
     s = s > sc ? s : sc;
   }
   off += s;
@@ -145,6 +154,8 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   if (!(c.newton_tol > 0.0) || c.newton_max < 1 || !(c.lin_rtol > 0.0) || c.lin_max < 1)
     return fail(nullptr, MLMC_ERR_ARG, "solver tolerances / iteration caps must be positive");
   if (!(c.s_t > 0.0) || !(c.s_l0 > 0.0)) return fail(nullptr, MLMC_ERR_ARG, "conductivities must be positive");
+  if (c.solver < MLMC_SOLVER_AUTO || c.solver > MLMC_SOLVER_CLUSTER)
+    return fail(nullptr, MLMC_ERR_ARG, "unknown solver layout");
 
   mlmc_ctx* ctx = new mlmc_ctx();
   ctx->cfg = c;
@@ -185,6 +196,7 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   sp.lin_rtol = c.precision == MLMC_PREC_MIXED ? fmax(c.lin_rtol, 1e-5) : c.lin_rtol;
   sp.lin_max = c.lin_max;
   sp.ls_full_step = 1e-6;
+  sp.step_max = __builtin_huge_val();   // set per level in solve_into
 
   // KL mode table and per-level 1D mode values at the cell centroids
   ctx->M = c.kl_modes;
@@ -296,11 +308,15 @@ extern "C" mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi,
 static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, double* t_act,
                               double* slab, mlmc_sample_info* info, char* ws, cudaStream_t st) {
   const LevelDesc& lv = ctx->lv[level];
-  bool mixed = ctx->cfg.precision == MLMC_PREC_MIXED;
+  bool mixed = level_mixed(ctx->cfg, lv);
   SolveWs w = solve_ws(lv, n, mixed);
   double* coef64 = (double*)(ws + w.coef64);
   float* coef32 = mixed ? (float*)(ws + w.coef32) : nullptr;
   CK(ctx, launch_assemble(lv, ctx->ph, Z, n, coef64, coef32, st));
+  ClusterPlan plan;
+  bool use_cluster = ctx->cfg.solver != MLMC_SOLVER_BLOCK && cluster_plan(lv, mixed, &plan);
+  if (ctx->cfg.solver == MLMC_SOLVER_CLUSTER && !use_cluster)
+    return fail(ctx, MLMC_ERR_ARG, "cluster layout requested but a sample of this level does not fit");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ctx->prof) {
     while (ctx->ev_pool.size() < ctx->ev_used + 2) {
@@ -312,9 +328,16 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     e1 = ctx->ev_pool[ctx->ev_used++];
     CK(ctx, cudaEventRecord(e0, st));
   }
-  CK(ctx, launch_solve(lv, ctx->ph, ctx->sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
-                       (double*)(ws + w.F), (double*)(ws + w.Ku), (double*)(ws + w.Kd),
-                       (void*)(ws + w.kr), t_act, info, ctx->d_cnt, st));
+  SolverParams sp = ctx->sp;
+  sp.lin_rtol = mixed ? fmax(ctx->cfg.lin_rtol, 1e-5) : ctx->cfg.lin_rtol;
+  sp.step_max = step_limit(ctx->cfg.c, ctx->cfg.a, lv.dt);
+  if (use_cluster)
+    CK(ctx, launch_solve_cluster(lv, ctx->ph, sp, mixed, plan, n, coef64, coef32, slab, t_act, info,
+                                 ctx->d_cnt, st));
+  else
+    CK(ctx, launch_solve(lv, ctx->ph, sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
+                         (double*)(ws + w.F), (double*)(ws + w.Ku), (double*)(ws + w.Kd),
+                         (void*)(ws + w.kr), t_act, info, ctx->d_cnt, st));
   if (ctx->prof) CK(ctx, cudaEventRecord(e1, st));
   ctx->launches += 2;
   return MLMC_OK;
@@ -327,7 +350,7 @@ extern "C" mlmc_status mlmc_solve(mlmc_ctx* ctx, int level, const double* Z, int
   if (bad_level(ctx, level)) return MLMC_ERR_ARG;
   if (n < 0 || n > 65535 || (n > 0 && (!Z || !t_act)))
     return fail(ctx, MLMC_ERR_ARG, "mlmc_solve: bad arguments");
-  size_t need = solve_ws(ctx->lv[level], n, ctx->cfg.precision == MLMC_PREC_MIXED).total;
+  size_t need = solve_ws(ctx->lv[level], n, level_mixed(ctx->cfg, ctx->lv[level])).total;
   if (!check_ws(ctx, ws, ws_bytes, need)) return MLMC_ERR_WORKSPACE;
   if (n == 0) return MLMC_OK;
   return solve_into(ctx, level, Z, n, t_act, slab, info, (char*)ws, (cudaStream_t)stream);

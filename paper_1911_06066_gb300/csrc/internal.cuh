@@ -40,7 +40,16 @@ struct SolverParams {
   double lin_rtol;
   int lin_max;
   double ls_full_step;   // max|d| below which the full Newton step is taken
+  double step_max;       // largest nodal move per Newton iteration (inf: none)
 };
+
+// Root-selection step limit: on strongly indefinite steps (c dt max r' > 2,
+// max r' = c((1+a)^2/3 - a)) no node moves by more than 0.1 per Newton
+// iteration; elsewhere steps are not limited.
+inline double step_limit(double c, double a, double dt) {
+  double rmax = c * ((1.0 + a) * (1.0 + a) / 3.0 - a);
+  return dt * rmax > 2.0 ? 0.1 : __builtin_huge_val();
+}
 
 // Number of stencil couplings per node (3^dim) and the centre index.
 __host__ __device__ inline int n_offsets(int dim) { return dim == 3 ? 27 : 9; }
@@ -82,6 +91,20 @@ cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverPar
                          double* slab, double* ubuf, double* F, double* Ku, double* Kd,
                          void* kr, double* t_act, mlmc_sample_info* info,
                          unsigned long long* counters, cudaStream_t st);
+// Cluster solver (solver_cluster.cu): C CTAs per sample, bands of H rows,
+// nt threads per CTA, couplings in shared memory or not, smem bytes per CTA.
+struct ClusterPlan {
+  int C, H, nt;
+  bool coef_smem;
+  size_t smem;
+};
+bool cluster_plan(const LevelDesc& lv, bool mixed, ClusterPlan* plan);
+size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt);
+cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
+                                 bool mixed, const ClusterPlan& pl, int n, const double* coef64,
+                                 const float* coef32, double* slab, double* t_act,
+                                 mlmc_sample_info* info, unsigned long long* counters,
+                                 cudaStream_t st);
 // counters (device, may be NULL): [0] non-converged solves, [1] CG iterations x
 // nodes, [2] Newton iterations x nodes, [3] CG truncations, [4] halvings.
 constexpr int N_COUNTERS = 5;

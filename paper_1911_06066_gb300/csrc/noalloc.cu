@@ -106,13 +106,16 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int level, con
   ph.Lz = c.dim == 3 ? c.L[2] : 1.0;
   ph.stim_r2 = c.stim_r * c.stim_r;
   for (int d = 0; d < 3; ++d) ph.stim_c[d] = c.stim_c[d];
-  const bool mixed = c.precision == MLMC_PREC_MIXED;
+  // FP32 inner solves only where c dt max r' <= 2, as in mlmc_solve
+  const double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
+  const bool mixed = c.precision == MLMC_PREC_MIXED && lv.dt * rmax <= 2.0;
   SolverParams sp;
   sp.newton_tol = c.newton_tol;
   sp.newton_max = c.newton_max;
   sp.lin_rtol = mixed ? fmax(c.lin_rtol, 1e-5) : c.lin_rtol;
   sp.lin_max = c.lin_max;
   sp.ls_full_step = 1e-6;
+  sp.step_max = step_limit(c.c, c.a, lv.dt);
 
   // scratch layout of mlmc_solve's workspace, carved from the static array
   size_t N = (size_t)nodes, NO = (size_t)n_offsets(c.dim), kr = mixed ? 4 : 8;

@@ -17,6 +17,9 @@
 //     first direction with p^T H p <= 0 (then the current iterate, or the
 //     preconditioned steepest-descent step in the first iteration);
 //   * stop once max|d| <= newton_tol (d still applied);
+//   * on strongly indefinite steps (c dt max r' > 2) start from
+//     alpha = min(1, 0.1 / max|d|), so no node moves by more than 0.1 per
+//     iteration and the selected root does not depend on rounding;
 //   * otherwise Armijo backtracking on E (sigma = 1e-4, halving, at most 40),
 //     the energy change summed node by node in a cancellation-free form; the
 //     full step is taken when max|d| <= ls_full_step.
@@ -211,6 +214,7 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
       for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) dmax_loc = fmax(dmax_loc, fabs((double)d[A]));
       const double dmax = block_max(dmax_loc, sh);
       double alpha = 1.0;
+      if (dmax > sp.step_max) alpha = sp.step_max / dmax;
       if (dmax > sp.newton_tol && dmax > sp.ls_full_step) {
         double gd_loc = 0.0;
         for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {

@@ -35,6 +35,9 @@ def ctx_for(w, precision=B.MLMC_PREC_FP64, **kw):
     return B.Context(B.make_config(w, precision, **kw))
 
 
+LAYOUTS = [pytest.param(B.MLMC_SOLVER_BLOCK, id="block"), pytest.param(B.MLMC_SOLVER_CLUSTER, id="cluster")]
+
+
 def ambiguous_nodes(slab, thr=0.5, eps=1e-6):
     """Nodes whose activation decision lies within eps of the threshold."""
     near = np.abs(slab - thr) < eps
@@ -42,8 +45,8 @@ def ambiguous_nodes(slab, thr=0.5, eps=1e-6):
 
 
 def compare_solve(w, level, sample_ids, seed=0, precision=B.MLMC_PREC_FP64, u_tol=U_TOL,
-                  t_tol=T_TOL):
-    ctx = ctx_for(w, precision)
+                  t_tol=T_TOL, solver=B.MLMC_SOLVER_AUTO):
+    ctx = ctx_for(w, precision, solver=solver)
     ids = torch.tensor(sample_ids, dtype=torch.int64)
     xi = ctx.xi(seed, level, ids)
     Z = ctx.kl_field(level, xi)
@@ -104,34 +107,69 @@ def test_kl_field(w, level):
 
 
 # ------------------------------------------------------------------ rows a3-a8
-def test_solve_mc2d_32_fp64():
+@pytest.mark.parametrize("solver", LAYOUTS)
+def test_solve_mc2d_32_fp64(solver):
     """The plain-MC workload (32x32, 64 steps, 16 modes): several samples."""
-    infos = compare_solve(W.MC2D_32, 0, [0, 1, 2, 15])
+    infos = compare_solve(W.MC2D_32, 0, [0, 1, 2, 15], solver=solver)
     assert max(i["truncations"] for i in infos) > 0      # the indefinite regime is exercised
 
 
-def test_solve_ragged_2d():
+@pytest.mark.parametrize("solver", LAYOUTS)
+def test_solve_ragged_2d(solver):
     w = small_workload(n0=(23, 37), m0=9, levels=1, M=10, stim_r=0.35, T=2.0)
-    compare_solve(w, 0, [0, 3])
+    compare_solve(w, 0, [0, 3], solver=solver)
 
 
-def test_solve_ragged_3d():
+@pytest.mark.parametrize("solver", LAYOUTS)
+def test_solve_ragged_3d(solver):
     w = small_workload(dim=3, n0=(6, 5, 3), m0=8, levels=1, M=12, ell=0.1, stim_r=0.35)
-    compare_solve(w, 0, [1, 2])
+    compare_solve(w, 0, [1, 2], solver=solver)
 
 
-def test_solve_mlmc2d_level1_fp64():
-    compare_solve(W.MLMC2D_3LVL, 1, [0, 9])
+@pytest.mark.parametrize("solver", LAYOUTS)
+def test_solve_mlmc2d_level1_fp64(solver):
+    """64^2 x 128 steps: two-CTA clusters (bands of 33 and 32 rows)."""
+    compare_solve(W.MLMC2D_3LVL, 1, [0, 9], solver=solver)
 
 
-def test_solve_slab3d_level0_fp64():
-    compare_solve(W.SLAB3D_4LVL, 0, [0])
+@pytest.mark.parametrize("solver", LAYOUTS)
+def test_solve_slab3d_level0_fp64(solver):
+    """32x32x8 x 32 steps: 16-CTA clusters, bands of single z-planes, one empty."""
+    compare_solve(W.SLAB3D_4LVL, 0, [0], solver=solver)
 
 
-def test_solve_mixed_spd_level_fp32_inner():
+@pytest.mark.parametrize("solver", LAYOUTS)
+def test_solve_mixed_spd_level_fp32_inner(solver):
     """Mixed precision at the finest 2D level (c dt max r' < 1): FP32 CG inside
     FP64 Newton converges to the same root."""
-    compare_solve(W.MLMC2D_3LVL, 2, [4], precision=B.MLMC_PREC_MIXED, u_tol=1e-7, t_tol=1e-4)
+    compare_solve(W.MLMC2D_3LVL, 2, [4], precision=B.MLMC_PREC_MIXED, u_tol=1e-7, t_tol=1e-4,
+                  solver=solver)
+
+
+def test_mixed_keeps_fp64_inner_solves_on_strongly_indefinite_levels():
+    """c dt max r' = 2.37 on the 32^2 level: the mixed configuration solves it
+    with FP64 CG, so its results equal the FP64 configuration's."""
+    w = W.MLMC2D_3LVL
+    outs = []
+    for prec in (B.MLMC_PREC_FP64, B.MLMC_PREC_MIXED):
+        ctx = ctx_for(w, prec)
+        Z = ctx.kl_field(0, ctx.xi(0, 0, torch.arange(24)))
+        t, _, info = ctx.solve(0, Z)
+        outs.append((t.cpu().numpy(), info.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_cluster_and_block_layouts_agree_full_size():
+    """128^2 x 256 steps, 8-CTA clusters vs one block per sample, FP64."""
+    w = W.MLMC2D_3LVL
+    res = []
+    for solver in (B.MLMC_SOLVER_BLOCK, B.MLMC_SOLVER_CLUSTER):
+        ctx = ctx_for(w, solver=solver)
+        Z = ctx.kl_field(2, ctx.xi(5, 2, torch.tensor([0, 1])))
+        t, _, info = ctx.solve(2, Z)
+        res.append(t.cpu().numpy())
+        assert all(i["status"] == 0 for i in B.info_dicts(info))
+    assert np.abs(res[0] - res[1]).max() <= T_TOL * w["T"]
 
 
 def test_slab_residual_matches_oracle():

@@ -40,7 +40,8 @@ def test_noalloc_matches_workspace_solve_twice():
     w = W.MLMC2D_3LVL
     for precision in (B.MLMC_PREC_FP64, B.MLMC_PREC_MIXED):
         cfg = B.make_config(w, precision)
-        ctx = B.Context(cfg)
+        # the reference solve uses the same kernel layout as the no-alloc path
+        ctx = B.Context(B.make_config(w, precision, solver=B.MLMC_SOLVER_BLOCK))
         calls = [(0, [0, 1, 2, 3]), (1, [5, 6])]     # two calls in a row, different sizes
         for level, ids in calls:
             Z = ctx.kl_field(level, ctx.xi(11, level, torch.tensor(ids)))
