@@ -50,8 +50,9 @@ typedef enum {
 
 typedef enum {
   MLMC_PREC_FP64 = 0,   /* every step in FP64                                       */
-  MLMC_PREC_MIXED = 1   /* FP32 Krylov inner solves on levels with c dt max r' <= 2
-                           (FP64 on the others); FP64 residual, update, QoI      */
+  MLMC_PREC_MIXED = 1   /* FP32 Krylov inner solves on levels with c dt max r' <=
+                           mixed_cdr_max (FP64 on the others); FP64 residual,
+                           update, QoI                                         */
 } mlmc_precision;
 
 /* Problem and solver configuration (plain data, copied by mlmc_create). */
@@ -77,6 +78,10 @@ typedef struct {
   double lin_rtol;       /* CG relative tolerance (FP64 inner solves)                */
   int lin_max;           /* CG iterations per Newton step                            */
   int solver;            /* mlmc_solver: kernel layout of the per-sample sweep        */
+  double mixed_cdr_max;  /* MLMC_PREC_MIXED uses FP32 inner solves only on levels with
+                            c dt max r' <= mixed_cdr_max (<= 0 selects the default 2) */
+  int cluster_size;      /* cluster layout: CTAs per sample (1, 2, 4, 8 or 16); 0 picks
+                            the smallest that fits shared memory                        */
 } mlmc_config;
 
 typedef enum {

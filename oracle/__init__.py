@@ -63,7 +63,7 @@ class Level(C.Structure):
 
 
 def make_level(dim, n, m, L, T, c, a, s_t, s_l0, theta0, theta1=None, stim_r=0.1,
-               stim_c=(0.0, 0.0, 0.0), newton_tol=1e-12, newton_max=200,
+               stim_c=(0.0, 0.0, 0.0), newton_tol=1e-12, newton_max=500,
                lin_rtol=1e-12, lin_max=5000):
     lv = Level()
     lv.dim = dim

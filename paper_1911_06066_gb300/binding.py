@@ -29,7 +29,8 @@ class mlmc_config(C.Structure):
                 ("theta1_deg", C.c_double), ("stim_r", C.c_double), ("stim_c", C.c_double * 3),
                 ("kl_sigma2", C.c_double), ("kl_ell", C.c_double), ("kl_modes", C.c_int),
                 ("precision", C.c_int), ("newton_tol", C.c_double), ("newton_max", C.c_int),
-                ("lin_rtol", C.c_double), ("lin_max", C.c_int), ("solver", C.c_int)]
+                ("lin_rtol", C.c_double), ("lin_max", C.c_int), ("solver", C.c_int),
+                ("mixed_cdr_max", C.c_double), ("cluster_size", C.c_int)]
 
 
 MLMC_SOLVER_AUTO, MLMC_SOLVER_BLOCK, MLMC_SOLVER_CLUSTER = 0, 1, 2
@@ -97,8 +98,9 @@ def exported_symbols():
             "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_solve_noalloc"]
 
 
-def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=200, lin_rtol=1e-12,
-                lin_max=5000, levels=None, solver=MLMC_SOLVER_AUTO):
+def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=500, lin_rtol=1e-12,
+                lin_max=5000, levels=None, solver=MLMC_SOLVER_AUTO, mixed_cdr_max=0.0,
+                cluster_size=0):
     """mlmc_config from a workload dictionary (see workloads.py)."""
     c = mlmc_config()
     c.dim = w["dim"]
@@ -116,6 +118,8 @@ def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=200, l
     c.precision = precision
     c.newton_tol, c.newton_max, c.lin_rtol, c.lin_max = newton_tol, newton_max, lin_rtol, lin_max
     c.solver = solver
+    c.mixed_cdr_max = mixed_cdr_max
+    c.cluster_size = cluster_size
     return c
 
 

@@ -71,13 +71,14 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // --------------------------------------------------------------- workspace
 // FP32 inner solves are used only where the step Jacobian is at most mildly
-// indefinite: c dt max r' <= 2, max r' = c((1+a)^2/3 - a).  On more strongly
-// indefinite levels the negative-curvature decisions of an FP32 CG can pick a
-// different root than FP64 (observed on the 32^2 / dt = 5/64 level).
+// indefinite: c dt max r' <= mixed_cdr_max (default 2), max r' =
+// c((1+a)^2/3 - a).  On strongly indefinite levels the negative-curvature
+// decisions of an FP32 CG can pick a different root than FP64.
 static bool level_mixed(const mlmc_config& c, const LevelDesc& lv) {
   if (c.precision != MLMC_PREC_MIXED) return false;
   double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
-  return lv.dt * rmax <= 2.0;
+  double lim = c.mixed_cdr_max > 0.0 ? c.mixed_cdr_max : 2.0;
+  return lv.dt * rmax <= lim;
 }
 
 struct SolveWs {
@@ -156,6 +157,9 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   if (!(c.s_t > 0.0) || !(c.s_l0 > 0.0)) return fail(nullptr, MLMC_ERR_ARG, "conductivities must be positive");
   if (c.solver < MLMC_SOLVER_AUTO || c.solver > MLMC_SOLVER_CLUSTER)
     return fail(nullptr, MLMC_ERR_ARG, "unknown solver layout");
+  if (c.cluster_size != 0 && c.cluster_size != 1 && c.cluster_size != 2 && c.cluster_size != 4 &&
+      c.cluster_size != 8 && c.cluster_size != 16)
+    return fail(nullptr, MLMC_ERR_ARG, "cluster_size must be 0, 1, 2, 4, 8 or 16");
 
   mlmc_ctx* ctx = new mlmc_ctx();
   ctx->cfg = c;
@@ -314,7 +318,8 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
   float* coef32 = mixed ? (float*)(ws + w.coef32) : nullptr;
   CK(ctx, launch_assemble(lv, ctx->ph, Z, n, coef64, coef32, st));
   ClusterPlan plan;
-  bool use_cluster = ctx->cfg.solver != MLMC_SOLVER_BLOCK && cluster_plan(lv, mixed, &plan);
+  bool use_cluster = ctx->cfg.solver != MLMC_SOLVER_BLOCK &&
+                     cluster_plan(lv, mixed, ctx->cfg.cluster_size, &plan);
   if (ctx->cfg.solver == MLMC_SOLVER_CLUSTER && !use_cluster)
     return fail(ctx, MLMC_ERR_ARG, "cluster layout requested but a sample of this level does not fit");
   cudaEvent_t e0 = nullptr, e1 = nullptr;

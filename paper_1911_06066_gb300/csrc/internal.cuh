@@ -98,7 +98,7 @@ struct ClusterPlan {
   bool coef_smem;
   size_t smem;
 };
-bool cluster_plan(const LevelDesc& lv, bool mixed, ClusterPlan* plan);
+bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan);
 size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt);
 cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                                  bool mixed, const ClusterPlan& pl, int n, const double* coef64,

@@ -106,9 +106,10 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int level, con
   ph.Lz = c.dim == 3 ? c.L[2] : 1.0;
   ph.stim_r2 = c.stim_r * c.stim_r;
   for (int d = 0; d < 3; ++d) ph.stim_c[d] = c.stim_c[d];
-  // FP32 inner solves only where c dt max r' <= 2, as in mlmc_solve
+  // FP32 inner solves only where c dt max r' <= mixed_cdr_max, as in mlmc_solve
   const double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
-  const bool mixed = c.precision == MLMC_PREC_MIXED && lv.dt * rmax <= 2.0;
+  const double cdr_lim = c.mixed_cdr_max > 0.0 ? c.mixed_cdr_max : 2.0;
+  const bool mixed = c.precision == MLMC_PREC_MIXED && lv.dt * rmax <= cdr_lim;
   SolverParams sp;
   sp.newton_tol = c.newton_tol;
   sp.newton_max = c.newton_max;

@@ -6,9 +6,9 @@
 // Mapping.  One cluster of C CTAs owns one sample.  The node grid is cut into
 // C bands of H whole rows (2D: rows of constant y; 3D: planes of constant z);
 // CTA r owns rows [rH, min((r+1)H, rows)).  Every per-node vector of the sweep
-// -- the FP64 state u (two slices), F, Ku, Kd and the CG vectors r, z, p, q, d,
-// diag, diag^-1 (FP64, or FP32 in the mixed path), and optionally the FP32 /
-// FP64 couplings used by the CG -- lives in the owning CTA's shared memory for
+// -- the FP64 state u (two slices) and residual F, the CG vectors r, z, p, q,
+// d, diag, diag^-1 (FP64, or FP32 in the mixed path), and, when they fit, the
+// couplings used by the CG in the CG's precision -- lives in the owning CTA's shared memory for
 // the whole time sweep.  A stencil touching the row above or below the band
 // reads the neighbour CTA's shared memory directly (DSMEM), so there is no
 // halo copy; the barrier that publishes a vector is the one the algorithm
@@ -87,33 +87,87 @@ __device__ __forceinline__ TA stencil_band(const Band& b, const View<TV>& v, int
   return y;
 }
 
-// Deterministic sum / max over the cluster; every thread of every CTA gets it.
-template <int NT>
-__device__ double cluster_reduce(double v, bool is_max, double* red, double* slot, int& par,
-                                 cg::cluster_group& cl, int C) {
-  v = is_max ? wmax(v) : wsum(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = red[0];
-    for (int w = 1; w < NT / 32; ++w) t = is_max ? fmax(t, red[w]) : t + red[w];
-    slot[par] = t;
+// Neighbour sum for a node whose 3^dim neighbours all lie inside the domain
+// and inside this CTA's band: constant local offsets.
+template <int DIM, typename TA, typename TV, typename CF>
+__device__ __forceinline__ TA stencil_fast(const TV* v, int a, int N0, int N01, CF c) {
+  TA y = 0;
+#pragma unroll
+  for (int o = 0; o < (DIM == 3 ? 27 : 9); ++o) {
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+    y += (TA)c(o) * (TA)v[a + dx + dy * N0 + dz * N01];
   }
-  double tot;
-  if (C == 1) {
-    __syncthreads();
-    tot = slot[par];
-  } else {
-    cl.sync();
-    tot = *cl.map_shared_rank(&slot[par], 0);
-    for (int q = 1; q < C; ++q) {
-      double x = *cl.map_shared_rank(&slot[par], q);
-      tot = is_max ? fmax(tot, x) : tot + x;
+  return y;
+}
+
+// Deterministic cluster-wide sums (op 0) or maxima (op 1, of non-negative
+// values) of K values per thread.  Warps reduce by butterfly shuffles in TP
+// (float in the mixed CG, double otherwise); warp 0 combines the CTA's warps
+// by a fixed shuffle tree; lane q then stores the CTA's K partials into
+// CTA q's slot[par][k][rank] (remote stores in parallel), one cluster barrier
+// publishes them, and warp 0 of every CTA combines the C partials by the same
+// fixed tree -- so every CTA obtains identical totals.  Lane 0 writes the
+// totals to bc[0..K) and calls post(bc) to derive further scalars in bc[K..8).
+// Every thread reads bc[] after the call returns.
+template <typename TP>
+__device__ __forceinline__ TP combine(TP x, TP y, int op) { return op ? (x > y ? x : y) : x + y; }
+
+template <int NT, typename TP, int K, typename POST>
+__device__ __forceinline__ void cluster_reduce(TP (&v)[K], int op, double* red, double* slot,
+                                               double* bc, int& par, cg::cluster_group& cl, int C,
+                                               int rank, POST post) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = combine(v[k], __shfl_xor_sync(0xffffffffu, v[k], o), op);
+    if (lane == 0) red[k * 32 + warp] = (double)v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    TP t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      t[k] = lane < NT / 32 ? (TP)red[k * 32 + lane] : (TP)0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t[k] = combine(t[k], __shfl_xor_sync(0xffffffffu, t[k], o), op);
+    }
+    if (C == 1) {
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) bc[k] = (double)t[k];
+        post(bc);
+      }
+    } else if (lane < C) {
+      double* dst = cl.map_shared_rank(slot + par * 64 + rank, lane);
+#pragma unroll
+      for (int k = 0; k < K; ++k) dst[k * 16] = (double)t[k];
     }
   }
+  if (C > 1) {
+    cl.sync();
+    if (warp == 0) {
+      TP t[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        t[k] = lane < C ? (TP)slot[par * 64 + k * 16 + lane] : (TP)0;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) t[k] = combine(t[k], __shfl_xor_sync(0xffffffffu, t[k], o), op);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) bc[k] = (double)t[k];
+        post(bc);
+      }
+    }
+  }
+  __syncthreads();
   par ^= 1;
-  return tot;
 }
+
+struct NoPost {
+  __device__ void operator()(double*) const {}
+};
 
 __device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl, int C) {
   if (C == 1) __syncthreads(); else cl.sync();
@@ -124,7 +178,7 @@ __device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl, int C) {
 // Byte offsets of the per-CTA shared-memory arrays; every array starts on a
 // 16-byte boundary.  Used by the kernel's carve-up and the host's sizing.
 struct SmemLayout {
-  size_t u0, u1, F, Ku, Kd, r, z, p, q, d, hm, pinv, cs, red, slot, total;
+  size_t u0, u1, F, r, z, p, q, d, hm, pinv, cs, code, red, slot, bc, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int dim, int nmax, int kr, bool coef_smem, int nt) {
@@ -136,12 +190,14 @@ __host__ __device__ inline SmemLayout smem_layout(int dim, int nmax, int kr, boo
     return at;
   };
   const size_t n8 = (size_t)nmax * 8, nk = (size_t)nmax * kr;
-  L.u0 = take(n8); L.u1 = take(n8); L.F = take(n8); L.Ku = take(n8); L.Kd = take(n8);
+  L.u0 = take(n8); L.u1 = take(n8); L.F = take(n8);
   L.r = take(nk); L.z = take(nk); L.p = take(nk); L.q = take(nk); L.d = take(nk);
   L.hm = take(nk); L.pinv = take(nk);
   L.cs = take(coef_smem ? (size_t)n_offsets(dim) * nk : 0);
-  L.red = take((size_t)(nt / 32) * 8);
-  L.slot = take(2 * 8);
+  L.code = take((size_t)nmax * 4);
+  L.red = take((size_t)4 * 32 * 8);
+  L.slot = take((size_t)2 * 4 * 16 * 8);
+  L.bc = take(8 * 8);
   L.total = o;
   return L;
 }
@@ -151,12 +207,13 @@ size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt)
   return smem_layout(dim, nmax, mixed ? 4 : 8, coef_smem, nt).total;
 }
 
-template <typename KR, int DIM, int NT>
+template <typename KR, int DIM, int NT, int NPT>
 __global__ void __launch_bounds__(NT, 1)
 solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict__ coef64,
                      const KR* __restrict__ coefK, int H, int coef_smem, double* slab,
                      double* t_act, mlmc_sample_info* info, unsigned long long* counters) {
   constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int CTR = DIM == 3 ? 13 : 4;
   cg::cluster_group cl = cg::this_cluster();
   Band b;
   b.C = (int)cl.num_blocks();
@@ -173,14 +230,14 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   const int N = (int)lv.nodes;
   const int base = b.row0 * b.rowlen;
   const int nmax = b.nmax;
+  const int N01 = b.N0 * b.N1;
+  const int tid = threadIdx.x;
 
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(DIM, nmax, (int)sizeof(KR), coef_smem != 0, NT);
   double* ubuf0 = (double*)(smem + L.u0);
   double* ubuf1 = (double*)(smem + L.u1);
   double* F = (double*)(smem + L.F);
-  double* Ku = (double*)(smem + L.Ku);
-  double* Kd = (double*)(smem + L.Kd);
   KR* r = (KR*)(smem + L.r);
   KR* z = (KR*)(smem + L.z);
   KR* p = (KR*)(smem + L.p);
@@ -191,6 +248,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   KR* cs = (KR*)(smem + L.cs);                             // couplings [NO][nmax] if coef_smem
   double* red = (double*)(smem + L.red);
   double* slot = (double*)(smem + L.slot);
+  double* bc = (double*)(smem + L.bc);
   int par = 0;
 
   const double* c64 = coef64 + (int64_t)s * NO * N;
@@ -199,16 +257,34 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   double* sl = slab ? slab + (int64_t)s * (lv.m + 1) * N : nullptr;
   const double dt = lv.dt, inv_dt = 1.0 / lv.dt;
 
+  // Per node: packed coordinates i | j << 11 | k << 22 and, in bit 31, whether
+  // every neighbour lies inside the domain and inside this band (then the
+  // stencil uses constant local offsets).
+  unsigned* code = (unsigned*)(smem + L.code);
+  for (int a = tid; a < b.nb; a += NT) {
+    const int lr = a / b.rowlen, inrow = a - lr * b.rowlen;
+    const int row = b.row0 + lr;
+    int i, j, k;
+    if (DIM == 3) { k = row; j = inrow / b.N0; i = inrow - j * b.N0; }
+    else { k = 0; j = row; i = inrow; }
+    bool in = i > 0 && i < b.N0 - 1 && j > 0 && j < b.N1 - 1 && (DIM == 2 || (k > 0 && k < b.N2 - 1));
+    bool fast = in && row > b.row0 && row < b.row1 - 1;
+    code[a] = (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22) | (fast ? 0x80000000u : 0u);
+  }
+#define CI(c) ((int)((c) & 2047u))
+#define CJ(c) ((int)(((c) >> 11) & 2047u))
+#define CK_(c) ((int)(((c) >> 22) & 511u))
+#define CFAST(c) (((c) & 0x80000000u) != 0u)
+
   cl.sync();   // every CTA of the cluster is resident before any DSMEM access
 
-  // couplings of the CG into shared memory; initial state
   if (coef_smem)
     for (int o = 0; o < NO; ++o)
-      for (int a = threadIdx.x; a < b.nb; a += NT) cs[o * nmax + a] = cKg[(int64_t)o * N + base + a];
-  for (int a = threadIdx.x; a < b.nb; a += NT) {
-    int A = base + a, i, j, k;
-    node_ijk(lv, A, i, j, k);
-    double x[3] = {i * lv.h[0], j * lv.h[1], k * lv.h[2]};
+      for (int a = tid; a < b.nb; a += NT) cs[o * nmax + a] = cKg[(int64_t)o * N + base + a];
+  for (int a = tid; a < b.nb; a += NT) {
+    const unsigned c = code[a];
+    const int A = base + a;
+    double x[3] = {CI(c) * lv.h[0], CJ(c) * lv.h[1], CK_(c) * lv.h[2]};
     double r2 = 0.0;
     for (int dd = 0; dd < DIM; ++dd) r2 += (x[dd] - ph.stim_c[dd]) * (x[dd] - ph.stim_c[dd]);
     double v = r2 < ph.stim_r2 ? 1.0 : 0.0;
@@ -220,7 +296,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   const View<KR> dv = make_view(cl, b, d);
   const View<double> uv0 = make_view(cl, b, ubuf0);
   const View<double> uv1 = make_view(cl, b, ubuf1);
-  auto c64f = [&](int A) { return [=](int o) { return c64[(int64_t)o * N + A]; }; };
+  const double rtol2 = sp.lin_rtol * sp.lin_rtol;
 
   int status = MLMC_OK, failed_step = 0;
   int newton_total = 0, cg_total = 0, trunc_total = 0, halvings = 0, max_newton = 0;
@@ -228,72 +304,101 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     double* u = (step & 1) ? ubuf1 : ubuf0;
     const double* up = (step & 1) ? ubuf0 : ubuf1;
     const View<double>& uv = (step & 1) ? uv1 : uv0;
-    for (int a = threadIdx.x; a < b.nb; a += NT) u[a] = up[a];
+    for (int a = tid; a < b.nb; a += NT) u[a] = up[a];
     cluster_barrier(cl, b.C);
     bool conv = false, lin_fail = false;
     int it;
     for (it = 1; it <= sp.newton_max; ++it) {
-      double rz_loc = 0.0;
-      for (int a = threadIdx.x; a < b.nb; a += NT) {
-        int A = base + a, i, j, k;
-        node_ijk(lv, A, i, j, k);
-        double mA = lumped_mass(lv, i, j, k);
-        double uA = u[a];
-        double ku = stencil_band<DIM, double>(b, uv, i, j, k, c64f(A));
-        Ku[a] = ku;
-        double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
+      // residual, Hessian diagonal and the CG start r = -F, z = P^-1 r, p = z, d = 0
+      KR rz_loc = 0;
+      for (int a = tid; a < b.nb; a += NT) {
+        const unsigned c = code[a];
+        const int A = base + a;
+        auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
+        const double ku = CFAST(c) ? stencil_fast<DIM, double>(u, a, b.N0, N01, c64A)
+                                   : stencil_band<DIM, double>(b, uv, CI(c), CJ(c), CK_(c), c64A);
+        const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c)), uA = u[a];
+        const double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
         F[a] = f;
-        double hmA = mA / dt - mA * rxn_d(ph, uA);
-        double pvv = 1.0 / fabs(hmA + c64[(int64_t)centre_offset(DIM) * N + A]);
-        KR rv = (KR)(-f);
-        KR zv = (KR)pvv * rv;
-        hm[a] = (KR)hmA;
-        pinv[a] = (KR)pvv;
+        // Hessian diagonal and Jacobi inverse in the CG's precision (the CG is
+        // the only user); no FP64 division on the per-node path
+        const KR uK = (KR)uA, mK = (KR)mA;
+        const KR rdK = (KR)ph.c * ((KR)(-3.0) * uK * uK + (KR)(2.0 * (1.0 + ph.a)) * uK - (KR)ph.a);
+        const KR hmA = mK * ((KR)inv_dt - rdK);
+        const KR pvv = (KR)1 / fabs(hmA + (KR)c64[(int64_t)CTR * N + A]);
+        const KR rv = (KR)(-f);
+        const KR zv = pvv * rv;
+        hm[a] = hmA;
+        pinv[a] = pvv;
         r[a] = rv; z[a] = zv; p[a] = zv; d[a] = (KR)0;
-        rz_loc += (double)(rv * zv);
+        rz_loc += rv * zv;
       }
-      double rz = cluster_reduce<NT>(rz_loc, false, red, slot, par, cl, b.C);
-      const double r0 = sqrt(rz);
+      {
+        KR v1[1] = {rz_loc};
+        cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+      }
+      double rz = bc[0];
+      const double rz_stop = rtol2 * rz;
       int cgi = 0;
       bool truncated = false;
-      if (r0 > 0.0) {
+      if (rz > 0.0) {
         bool ok = false;
         for (cgi = 1; cgi <= sp.lin_max; ++cgi) {
           KR pq_loc = 0;
-          for (int a = threadIdx.x; a < b.nb; a += NT) {
-            int A = base + a, i, j, k;
-            node_ijk(lv, A, i, j, k);
+          for (int a = tid; a < b.nb; a += NT) {
+            const unsigned c = code[a];
+            const int A = base + a;
             KR hp;
-            if (coef_smem)
-              hp = stencil_band<DIM, KR>(b, pv, i, j, k, [=](int o) { return cs[o * nmax + a]; });
-            else
-              hp = stencil_band<DIM, KR>(b, pv, i, j, k, [=](int o) { return cKg[(int64_t)o * N + A]; });
-            KR qv = hp + hm[a] * p[a];
+            if (coef_smem) {
+              auto cf = [=](int o) { return cs[o * nmax + a]; };
+              hp = CFAST(c) ? stencil_fast<DIM, KR>(p, a, b.N0, N01, cf)
+                            : stencil_band<DIM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
+            } else {
+              auto cf = [=](int o) { return cKg[(int64_t)o * N + A]; };
+              hp = CFAST(c) ? stencil_fast<DIM, KR>(p, a, b.N0, N01, cf)
+                            : stencil_band<DIM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
+            }
+            const KR pa = p[a];
+            const KR qv = hp + hm[a] * pa;
             q[a] = qv;
-            pq_loc += p[a] * qv;
+            pq_loc += pa * qv;
           }
-          double pq = cluster_reduce<NT>((double)pq_loc, false, red, slot, par, cl, b.C);
+          const double rzc = rz;
+          {
+            KR v1[1] = {pq_loc};
+            cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, [=](double* o) {
+              o[1] = o[0] > 0.0 ? (double)((KR)rzc / (KR)o[0]) : 0.0;
+            });
+          }
+          const double pq = bc[0];
           if (pq <= 0.0) {
             truncated = true;
             if (cgi == 1)
-              for (int a = threadIdx.x; a < b.nb; a += NT) d[a] = z[a];
+              for (int a = tid; a < b.nb; a += NT) d[a] = z[a];
             ok = true;
             break;
           }
-          const KR alpha = (KR)(rz / pq);
+          const KR alpha = (KR)bc[1];
           KR rzn_loc = 0;
-          for (int a = threadIdx.x; a < b.nb; a += NT) {
+          for (int a = tid; a < b.nb; a += NT) {
             d[a] += alpha * p[a];
-            KR rv = r[a] - alpha * q[a];
-            KR zv = pinv[a] * rv;
+            const KR rv = r[a] - alpha * q[a];
+            const KR zv = pinv[a] * rv;
             r[a] = rv;
             z[a] = zv;
             rzn_loc += rv * zv;
           }
-          double rz_new = cluster_reduce<NT>((double)rzn_loc, false, red, slot, par, cl, b.C);
-          if (sqrt(rz_new) <= sp.lin_rtol * r0) { ok = true; break; }
-          const KR beta = (KR)(rz_new / rz);
-          for (int a = threadIdx.x; a < b.nb; a += NT) p[a] = z[a] + beta * p[a];
+          {
+            KR v1[1] = {rzn_loc};
+            cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, [=](double* o) {
+              o[1] = (double)((KR)o[0] / (KR)rzc);
+              o[2] = o[0] <= rz_stop ? 1.0 : 0.0;
+            });
+          }
+          const double rz_new = bc[0];
+          if (bc[2] != 0.0) { ok = true; break; }
+          const KR beta = (KR)bc[1];
+          for (int a = tid; a < b.nb; a += NT) p[a] = z[a] + beta * p[a];
           cluster_barrier(cl, b.C);
           rz = rz_new;
         }
@@ -302,39 +407,58 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       cg_total += cgi;
       trunc_total += truncated ? 1 : 0;
       if (lin_fail) break;
-      double dm_loc = 0.0;
-      for (int a = threadIdx.x; a < b.nb; a += NT) dm_loc = fmax(dm_loc, fabs((double)d[a]));
-      const double dmax = cluster_reduce<NT>(dm_loc, true, red, slot, par, cl, b.C);
+      KR dm_loc = 0;
+      for (int a = tid; a < b.nb; a += NT) dm_loc = fmax(dm_loc, fabs(d[a]));   // exact in KR
+      {
+        KR v1[1] = {dm_loc};
+        cluster_reduce<NT, KR, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+      }
+      const double dmax = bc[0];
       double alpha = 1.0;
       if (dmax > sp.step_max) alpha = sp.step_max / dmax;
       if (dmax > sp.newton_tol && dmax > sp.ls_full_step) {
-        double gd_loc = 0.0;
-        for (int a = threadIdx.x; a < b.nb; a += NT) {
-          int A = base + a, i, j, k;
-          node_ijk(lv, A, i, j, k);
-          Kd[a] = stencil_band<DIM, double>(b, dv, i, j, k, c64f(A));
-          gd_loc += F[a] * (double)d[a];
+        // The step energy is a quartic polynomial in the step length (R is a
+        // quartic), so for every trial length al
+        //   E(u + al d) - E(u) = al g.d + al^2 d.Hd / 2 - al^3 P3 - al^4 P4,
+        //   P3 = sum_i m_i r2(u_i) d_i^3 / 6,  P4 = sum_i m_i r3 d_i^4 / 24,
+        // with r2 = r'' = c(2(1+a) - 6u) and r3 = r''' = -6c; one pass over the
+        // nodes gives the four sums and thread 0 runs every Armijo test.
+        double v4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int a = tid; a < b.nb; a += NT) {
+          const unsigned c = code[a];
+          const int A = base + a;
+          auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
+          const double kd = CFAST(c) ? stencil_fast<DIM, double>(d, a, b.N0, N01, c64A)
+                                     : stencil_band<DIM, double>(b, dv, CI(c), CJ(c), CK_(c), c64A);
+          const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c));
+          const double uA = u[a], da = (double)d[a], d2 = da * da;
+          const double r1 = ph.c * (-3.0 * uA * uA + 2.0 * (1.0 + ph.a) * uA - ph.a);
+          const double r2 = ph.c * (2.0 * (1.0 + ph.a) - 6.0 * uA);
+          v4[0] += F[a] * da;
+          v4[1] += mA * (inv_dt - r1) * d2 + da * kd;
+          v4[2] += mA * r2 * d2 * da;
+          v4[3] += mA * d2 * d2;
         }
-        const double gd = cluster_reduce<NT>(gd_loc, false, red, slot, par, cl, b.C);
-        for (int h = 0; h < 40; ++h) {
-          double e_loc = 0.0;
-          for (int a = threadIdx.x; a < b.nb; a += NT) {
-            int A = base + a, i, j, k;
-            node_ijk(lv, A, i, j, k);
-            double mA = lumped_mass(lv, i, j, k);
-            double uA = u[a], w = alpha * (double)d[a], v = uA + w;
-            double sm = v + uA, q2 = v * v + uA * uA, q3 = v * v + v * uA + uA * uA;
-            double rdiff = ph.c * w * (-sm * q2 / 4.0 + (1.0 + ph.a) * q3 / 3.0 - ph.a * sm / 2.0);
-            e_loc += mA * w * (2.0 * (uA - up[a]) + w) / (2.0 * dt) + w * Ku[a] +
-                     0.5 * w * alpha * Kd[a] - mA * rdiff;
-          }
-          double dE = cluster_reduce<NT>(e_loc, false, red, slot, par, cl, b.C);
-          if (dE <= 1e-4 * alpha * gd) break;
-          alpha *= 0.5;
-          ++halvings;
-        }
+        const double alpha0 = alpha, cc = ph.c;
+        cluster_reduce<NT, double, 4>(v4, 0, red, slot, bc, par, cl, b.C, b.rank,
+                                      [=](double* o) {
+                                        const double gd = o[0], dHd = o[1];
+                                        const double P3 = o[2] / 6.0, P4 = -6.0 * cc * o[3] / 24.0;
+                                        double al = alpha0;
+                                        int h = 0;
+                                        for (; h < 40; ++h) {
+                                          const double dE = al * gd + 0.5 * al * al * dHd -
+                                                            al * al * al * P3 - al * al * al * al * P4;
+                                          if (dE <= 1e-4 * al * gd) break;
+                                          al *= 0.5;
+                                        }
+                                        o[4] = al;
+                                        o[5] = (double)h;
+                                      });
+        alpha = bc[4];
+        halvings += (int)bc[5];
       }
-      for (int a = threadIdx.x; a < b.nb; a += NT) u[a] += alpha * (double)d[a];
+      for (int a = tid; a < b.nb; a += NT) u[a] += alpha * (double)d[a];
       cluster_barrier(cl, b.C);
       if (dmax <= sp.newton_tol) { conv = true; break; }
     }
@@ -342,8 +466,8 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     newton_total += used;
     max_newton = used > max_newton ? used : max_newton;
     if (!conv) { status = MLMC_ERR_NOT_CONVERGED; failed_step = step; break; }
-    for (int a = threadIdx.x; a < b.nb; a += NT) {
-      int A = base + a;
+    for (int a = tid; a < b.nb; a += NT) {
+      const int A = base + a;
       if (ta[A] < 0.0 && u[a] >= 0.5) {
         double uo = up[a];
         ta[A] = (double)(step - 1) * dt + dt * (0.5 - uo) / (u[a] - uo);
@@ -351,9 +475,13 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       if (sl) sl[(int64_t)step * N + A] = u[a];
     }
   }
-  for (int a = threadIdx.x; a < b.nb; a += NT)
+#undef CI
+#undef CJ
+#undef CK_
+#undef CFAST
+  for (int a = tid; a < b.nb; a += NT)
     if (ta[base + a] < 0.0) ta[base + a] = lv.T;
-  if (b.rank == 0 && threadIdx.x == 0) {
+  if (b.rank == 0 && tid == 0) {
     if (counters) {
       if (status != MLMC_OK) atomicAdd(counters, 1ull);
       atomicAdd(counters + 1, (unsigned long long)cg_total * (unsigned long long)N);
@@ -372,17 +500,18 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   cl.sync();   // no CTA leaves while a neighbour may still read its shared memory
 }
 
-// Launch plan: the smallest cluster whose bands fit the shared memory, and the
-// block size.  Returns false when no cluster size up to 16 fits.
-bool cluster_plan(const LevelDesc& lv, bool mixed, ClusterPlan* plan) {
+// Launch plan: the smallest cluster whose bands fit the shared memory (or the
+// requested size want_C), and the block size.  Returns false when it does not fit.
+bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan) {
   const int rowlen = lv.dim == 3 ? lv.N[0] * lv.N[1] : lv.N[0];
   const int nrows = lv.dim == 3 ? lv.N[2] : lv.N[1];
-  const size_t limit = 200 * 1024;
+  const size_t limit = 224 * 1024;
   for (int C = 1; C <= 16; C *= 2) {
+    if (want_C && C != want_C) continue;
     int H = (nrows + C - 1) / C;
     int nmax = H * rowlen;
-    if (nmax > 2400 && C < 16) continue;
-    int nt = nmax <= 1200 ? 512 : 1024;
+    if (nmax > 2400) continue;           // 512 threads x at most 5 nodes each
+    int nt = 512;
     bool coef = cluster_smem_bytes(lv.dim, nmax, mixed, true, nt) <= limit;
     size_t bytes = cluster_smem_bytes(lv.dim, nmax, mixed, coef, nt);
     if (bytes > limit) continue;
@@ -392,12 +521,12 @@ bool cluster_plan(const LevelDesc& lv, bool mixed, ClusterPlan* plan) {
   return false;
 }
 
-template <typename KR, int DIM, int NT>
+template <typename KR, int DIM, int NT, int NPT>
 static cudaError_t launch_one(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                               const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
                               double* slab, double* t_act, mlmc_sample_info* info,
                               unsigned long long* counters, cudaStream_t st) {
-  auto kern = solve_cluster_kernel<KR, DIM, NT>;
+  auto kern = solve_cluster_kernel<KR, DIM, NT, NPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return e;
   if (pl.C > 8) {
@@ -425,9 +554,7 @@ static cudaError_t launch_nt(const LevelDesc& lv, const Physics& ph, const Solve
                              const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
                              double* slab, double* t_act, mlmc_sample_info* info,
                              unsigned long long* counters, cudaStream_t st) {
-  if (pl.nt == 1024)
-    return launch_one<KR, DIM, 1024>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info, counters, st);
-  return launch_one<KR, DIM, 512>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info, counters, st);
+  return launch_one<KR, DIM, 512, 5>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info, counters, st);
 }
 
 cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,

@@ -116,8 +116,10 @@ def test_solve_mc2d_32_fp64(solver):
 
 @pytest.mark.parametrize("solver", LAYOUTS)
 def test_solve_ragged_2d(solver):
-    w = small_workload(n0=(23, 37), m0=9, levels=1, M=10, stim_r=0.35, T=2.0)
-    compare_solve(w, 0, [0, 3], solver=solver)
+    """24 x 38 nodes (ragged against the block sizes), dt = 0.1: c dt max r' = 3,
+    so the step limit and negative-curvature truncation are exercised."""
+    w = small_workload(n0=(23, 37), m0=20, levels=1, M=10, stim_r=0.35, T=2.0)
+    compare_solve(w, 0, [0, 3, 4], solver=solver)
 
 
 @pytest.mark.parametrize("solver", LAYOUTS)
@@ -202,12 +204,49 @@ def test_activation_kernel_matches_oracle():
     assert np.abs(t - to).max() <= 1e-14 * lv.T
 
 
+def independent_step_checks(lv, Z, slab):
+    """Rebuilt (3-point Gauss) residual of every step and the smallest
+    eigenvalue of every step Hessian, for a slab produced by the CUDA path."""
+    from test_oracle_solve import independent_operators
+    mass, K = independent_operators(lv, Z)
+    dt = lv.T / lv.m
+    res, lam = 0.0, np.inf
+    for k in range(1, lv.m + 1):
+        u, up = slab[k], slab[k - 1]
+        F = mass / dt * (u - up) + K @ u - mass * lv.c * u * (1 - u) * (u - lv.a)
+        res = max(res, np.abs(F / mass).max())
+        rp = lv.c * (-3 * u * u + 2 * (1 + lv.a) * u - lv.a)
+        lam = min(lam, np.linalg.eigvalsh(K + np.diag(mass / dt - mass * rp)).min())
+    return res, lam
+
+
+@pytest.mark.parametrize("solver", LAYOUTS)
+def test_strongly_indefinite_steps_give_valid_roots(solver):
+    """c dt max r' = 5.7 (far stiffer than any workload level): which of the
+    step's roots Newton reaches can depend on rounding, so the CUDA result is
+    checked for what makes it a valid result of the method -- every step
+    satisfies its residual and is a local minimum of its step energy."""
+    w = small_workload(n0=(6, 6), m0=8, levels=1, M=8, stim_r=0.3, s_l0=0.02, s_t=0.005,
+                       sigma2=0.25, T=1.5)
+    ctx = ctx_for(w, solver=solver)
+    ids = [0, 1, 5]
+    Z = ctx.kl_field(0, ctx.xi(9, 0, torch.tensor(ids)))
+    t, slab, info = ctx.solve(0, Z, slab=True)
+    lv = oracle_level(w, 0)
+    for r in range(len(ids)):
+        assert B.info_dicts(info)[r]["status"] == 0
+        res, lam = independent_step_checks(lv, Z[r].cpu().numpy(), slab[r].cpu().numpy())
+        assert res < 1e-9 and lam > 0.0, (res, lam)
+
+
 # ------------------------------------------------------------------ rows a9-a10
 def test_sample_level_pairs():
-    w = small_workload(n0=(6, 6), m0=8, levels=3, M=8, stim_r=0.3, s_l0=0.02, s_t=0.005,
+    """Three levels with fronts that cross the coarse grids (c dt max r' = 1.9,
+    0.95, 0.47: the regime of the workloads' finer levels)."""
+    w = small_workload(n0=(6, 6), m0=24, levels=3, M=8, stim_r=0.3, s_l0=0.02, s_t=0.005,
                        sigma2=0.25, T=1.5)
-    lvs = oracle_levels(w, newton_max=200)
-    ctx = ctx_for(w, newton_max=200)
+    lvs = oracle_levels(w, newton_max=500)
+    ctx = ctx_for(w, newton_max=500)
     ids = [0, 1, 5]
     for level in range(3):
         y, y2, tf, tc, info = ctx.sample_level(level, 9, torch.tensor(ids), want_maps=True)
@@ -252,8 +291,8 @@ def test_accumulate_and_estimate():
 def test_run_matches_oracle_mlmc():
     w = small_workload(n0=(4, 4), m0=16, levels=2, M=8, stim_r=0.3, s_l0=0.02, s_t=0.005,
                        sigma2=0.25, T=1.5)
-    lvs = oracle_levels(w, newton_max=200)
-    ctx = ctx_for(w, newton_max=200)
+    lvs = oracle_levels(w, newton_max=500)
+    ctx = ctx_for(w, newton_max=500)
     N = [24, 10]
     res = ctx.run(N, seed=1, batch=7)
     est = O.mlmc_estimate(lvs, w["sigma2"], w["ell"], w["M"], 1, N)

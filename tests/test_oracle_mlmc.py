@@ -82,7 +82,7 @@ def test_mlmc_unbiased_against_brute_force_mc():
     the sum of their standard errors (fixed seeds, CLT bound)."""
     w = small_workload(n0=(4, 4), m0=16, levels=2, M=8, stim_r=0.3, s_l0=0.02, s_t=0.005,
                        sigma2=0.25, T=1.5)
-    lvs = oracle_levels(w, newton_max=200)
+    lvs = oracle_levels(w, newton_max=500)
     est = O.mlmc_estimate(lvs, w["sigma2"], w["ell"], w["M"], 1, [160, 40], threads=4)
     # plain MC on level 1 with its own (independent) stream: level-pair index 7
     T1 = []
