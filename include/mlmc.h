@@ -197,19 +197,24 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean
 /* Whole MLMC run with fixed sample counts (host N_l[n_levels]): for each level
  * l, sample ids 0..N_l-1 in batches of at most `batch` pairs, mlmc_sample_level
  * + mlmc_accumulate; then mlmc_estimate into the host outputs (as above;
- * synchronises the stream).  ws: mlmc_run_workspace_bytes(ctx, batch) bytes.
- * C_l (host [n_levels], may be NULL): device time per pair of each level, s.
- * stats (host [8], may be NULL): device ms spent in the per-sample solve
- * kernel (CUDA events around its launches), its launch count, CG and Newton
- * iterations summed over samples and weighted by the nodes of their grid,
- * CG truncations, line-search halvings, non-converged solves, and the total
- * number of kernels launched.  Returns MLMC_ERR_NOT_CONVERGED (outputs still
+ * synchronises the stream).  Levels run concurrently on streams owned by the
+ * context (ordered after the work already on `stream`; `stream` waits for
+ * them); within a level the fine and coarse solves of a batch run
+ * concurrently.  ws: mlmc_run_workspace_bytes(ctx, N_l, batch) bytes.
+ * C_l (host [n_levels], may be NULL): wall time of each level's work divided
+ * by N_l (levels overlap, so this is not an exclusive cost).
+ * stats (host [9], may be NULL): device ms spent in the per-sample solve
+ * kernel (CUDA events around its launches, summed), its launch count, CG and
+ * Newton iterations summed over samples and weighted by the nodes of their
+ * grid, CG truncations, line-search halvings, non-converged solves, the total
+ * number of kernels launched, and the node-weighted CG iterations run in FP64.  Returns MLMC_ERR_NOT_CONVERGED (outputs still
  * written) if any solve failed. */
 mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed, int batch, void* ws,
                      size_t ws_bytes, double* mean, double* var, double* V_l, double* C_l,
                      double* rmse, double* stats, void* stream);
-/* Workspace bytes for mlmc_run with the given batch. */
-mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, int batch, size_t* bytes);
+/* Workspace bytes for mlmc_run with the given counts (host N_l) and batch. */
+mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, const int64_t* N_l, int batch,
+                                     size_t* bytes);
 
 /* Allocation-free variant of mlmc_solve (the paper has no counterpart; this is
  * a deployment aid).  For callers that may not allocate device memory -- for

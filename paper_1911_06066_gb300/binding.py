@@ -79,7 +79,7 @@ def lib():
             "mlmc_reset": ([vp, vp], ip),
             "mlmc_estimate": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], ip),
             "mlmc_run": ([vp, vp, u64, ip, vp, sz, vp, vp, vp, vp, vp, vp, vp], ip),
-            "mlmc_run_workspace_bytes": ([vp, ip, C.POINTER(sz)], ip),
+            "mlmc_run_workspace_bytes": ([vp, vp, ip, C.POINTER(sz)], ip),
             "mlmc_solve_noalloc": ([C.POINTER(mlmc_config), ip, vp, ip, vp, vp, vp], ip),
         }
         for name, (args, res) in sig.items():
@@ -171,9 +171,11 @@ class Context:
         self._check(lib().mlmc_workspace_bytes(self.h, level, n, C.byref(b)))
         return b.value
 
-    def run_workspace_bytes(self, batch):
+    def run_workspace_bytes(self, N_l, batch):
         b = C.c_size_t()
-        self._check(lib().mlmc_run_workspace_bytes(self.h, batch, C.byref(b)))
+        Nh = np.ascontiguousarray(N_l, np.int64)
+        self._check(lib().mlmc_run_workspace_bytes(self.h, Nh.ctypes.data_as(C.c_void_p), batch,
+                                                   C.byref(b)))
         return b.value
 
     def workspace(self, nbytes, key="ws"):
@@ -280,15 +282,15 @@ class Context:
         n0, _, _ = self.level_info(0)
         Nh = np.ascontiguousarray(N_l, np.int64)
         mean, var, V, Cl = np.zeros(n0), np.zeros(n0), np.zeros(L), np.zeros(L)
-        stats = np.zeros(8)
+        stats = np.zeros(9)
         rmse = C.c_double()
-        nb = self.run_workspace_bytes(batch)
+        nb = self.run_workspace_bytes(Nh, batch)
         ws = self.workspace(nb, key="run")
         dp = lambda a: a.ctypes.data_as(C.c_void_p)
         self._check(lib().mlmc_run(self.h, dp(Nh), seed, batch, _p(ws), ws.numel(), dp(mean), dp(var),
                                    dp(V), dp(Cl), C.byref(rmse), dp(stats), _stream(stream)))
         keys = ("solve_ms", "solve_launches", "cg_node_iters", "newton_node_iters", "truncations",
-                "halvings", "failed", "launches")
+                "halvings", "failed", "launches", "cg64_node_iters")
         return dict(mean=mean, var=var, V_l=V, C_l=Cl, rmse=rmse.value, N_l=Nh,
                     stats=dict(zip(keys, stats.tolist())))
 

@@ -36,6 +36,12 @@ struct mlmc_ctx {
   double* d_est = nullptr;        // estimate output
   unsigned long long* d_cnt = nullptr;  // solver counters (see N_COUNTERS)
   int64_t N_acc[MLMC_MAX_LEVELS] = {};
+  // streams for concurrent solves: [2l] fine / [2l+1] coarse solves of level
+  // l inside mlmc_run; aux_pub for the coarse solve of mlmc_sample_level
+  cudaStream_t lvl_stream[2 * MLMC_MAX_LEVELS] = {};
+  cudaStream_t aux_pub = nullptr;
+  std::vector<cudaEvent_t> sync_pool;   // ordering-only events
+  size_t sync_used = 0;
   // launch accounting and solve-kernel timing, active inside mlmc_run
   bool prof = false;
   long launches = 0;
@@ -101,7 +107,7 @@ static SolveWs solve_ws(const LevelDesc& lv, int n, bool mixed) {
 }
 
 struct PairWs {
-  size_t xi, Zf, Zc, tf, tc, info, solve, total;
+  size_t xi, Zf, Zc, tf, tc, info, solve_f, solve_c, total;
 };
 
 static PairWs pair_ws(const mlmc_ctx* c, int level, int n) {
@@ -114,13 +120,9 @@ static PairWs pair_ws(const mlmc_ctx* c, int level, int n) {
   w.tf = off; off += align256((size_t)n * lf.nodes * 8);
   w.tc = off; off += level > 0 ? align256((size_t)n * c->lv[level - 1].nodes * 8) : 0;
   w.info = off; off += align256((size_t)2 * n * sizeof(mlmc_sample_info));
-  w.solve = off;
-  size_t s = solve_ws(lf, n, level_mixed(c->cfg, lf)).total;
-  if (level > 0) {
-    size_t sc = solve_ws(c->lv[level - 1], n, level_mixed(c->cfg, c->lv[level - 1])).total;
-    s = s > sc ? s : sc;
-  }
-  off += s;
+  w.solve_f = off; off += solve_ws(lf, n, level_mixed(c->cfg, lf)).total;
+  w.solve_c = off;
+  if (level > 0) off += solve_ws(c->lv[level - 1], n, level_mixed(c->cfg, c->lv[level - 1])).total;
   w.total = off;
   return w;
 }
@@ -238,6 +240,11 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   if ((e = cudaMalloc(&ctx->d_cnt, sizeof(unsigned long long) * N_COUNTERS)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
   if ((e = cudaMemset(ctx->d_acc, 0, sizeof(double) * 3 * L * n0)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
   if ((e = cudaMemset(ctx->d_cnt, 0, sizeof(unsigned long long) * N_COUNTERS)) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
+  for (int i = 0; i < 2 * L; ++i)
+    if ((e = cudaStreamCreateWithFlags(&ctx->lvl_stream[i], cudaStreamNonBlocking)) != cudaSuccess)
+      return cleanup_fail(e, "cudaStreamCreate");
+  if ((e = cudaStreamCreateWithFlags(&ctx->aux_pub, cudaStreamNonBlocking)) != cudaSuccess)
+    return cleanup_fail(e, "cudaStreamCreate");
   *out = ctx;
   return MLMC_OK;
 }
@@ -253,11 +260,30 @@ extern "C" void mlmc_destroy(mlmc_ctx* ctx) {
   cudaFree(ctx->d_est);
   cudaFree(ctx->d_cnt);
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : ctx->sync_pool) cudaEventDestroy(ev);
+  for (int i = 0; i < 2 * MLMC_MAX_LEVELS; ++i)
+    if (ctx->lvl_stream[i]) cudaStreamDestroy(ctx->lvl_stream[i]);
+  if (ctx->aux_pub) cudaStreamDestroy(ctx->aux_pub);
   delete ctx;
 }
 
 extern "C" const char* mlmc_last_error(const mlmc_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+// Make `waiter` wait for the work enqueued so far on `src` (an ordering-only
+// event from the context's pool).
+static mlmc_status order_after(mlmc_ctx* ctx, cudaStream_t src, cudaStream_t waiter) {
+  if (src == waiter) return MLMC_OK;
+  if (ctx->sync_used == ctx->sync_pool.size()) {
+    cudaEvent_t ev;
+    CK(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ctx->sync_pool.push_back(ev);
+  }
+  cudaEvent_t ev = ctx->sync_pool[ctx->sync_used++];
+  CK(ctx, cudaEventRecord(ev, src));
+  CK(ctx, cudaStreamWaitEvent(waiter, ev, 0));
+  return MLMC_OK;
 }
 
 static bool bad_level(mlmc_ctx* ctx, int level) {
@@ -392,28 +418,34 @@ extern "C" mlmc_status mlmc_activation(mlmc_ctx* ctx, int level, const double* s
   return MLMC_OK;
 }
 
+// One batch of level-l pairs: xi and both fields on st_f, the fine solve on
+// st_f and the coarse solve concurrently on st_c, then the differences on st_f.
 static mlmc_status sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* ids,
                                      int n, double* y, double* y2, double* t_fine, double* t_coarse,
-                                     mlmc_sample_info* info, char* ws, cudaStream_t st) {
+                                     mlmc_sample_info* info, char* ws, cudaStream_t st_f,
+                                     cudaStream_t st_c) {
   PairWs w = pair_ws(ctx, level, n);
   double* xi = (double*)(ws + w.xi);
   double* Zf = (double*)(ws + w.Zf);
   double* tf = t_fine ? t_fine : (double*)(ws + w.tf);
   mlmc_sample_info* inf = info ? info : (mlmc_sample_info*)(ws + w.info);
-  CK(ctx, launch_xi(seed, level, ids, n, ctx->M, xi, st));
+  CK(ctx, launch_xi(seed, level, ids, n, ctx->M, xi, st_f));
   ctx->launches += 1;
   mlmc_status r;
-  if ((r = mlmc_kl_field(ctx, level, xi, n, Zf, st)) != MLMC_OK) return r;
-  if ((r = solve_into(ctx, level, Zf, n, tf, nullptr, inf, ws + w.solve, st)) != MLMC_OK) return r;
+  if ((r = mlmc_kl_field(ctx, level, xi, n, Zf, st_f)) != MLMC_OK) return r;
   double* tc = nullptr;
   if (level > 0) {
     double* Zc = (double*)(ws + w.Zc);
     tc = t_coarse ? t_coarse : (double*)(ws + w.tc);
-    if ((r = mlmc_kl_field(ctx, level - 1, xi, n, Zc, st)) != MLMC_OK) return r;
-    if ((r = solve_into(ctx, level - 1, Zc, n, tc, nullptr, inf + n, ws + w.solve, st)) != MLMC_OK) return r;
+    if ((r = mlmc_kl_field(ctx, level - 1, xi, n, Zc, st_f)) != MLMC_OK) return r;
+    if ((r = order_after(ctx, st_f, st_c)) != MLMC_OK) return r;
+    if ((r = solve_into(ctx, level - 1, Zc, n, tc, nullptr, inf + n, ws + w.solve_c, st_c)) != MLMC_OK)
+      return r;
   }
+  if ((r = solve_into(ctx, level, Zf, n, tf, nullptr, inf, ws + w.solve_f, st_f)) != MLMC_OK) return r;
+  if (level > 0 && (r = order_after(ctx, st_c, st_f)) != MLMC_OK) return r;
   CK(ctx, launch_pair_diff(ctx->lv[0], ctx->lv[level], level > 0 ? &ctx->lv[level - 1] : nullptr, tf,
-                           tc, n, y, y2, st));
+                           tc, n, y, y2, st_f));
   ctx->launches += 1;
   return MLMC_OK;
 }
@@ -428,8 +460,9 @@ extern "C" mlmc_status mlmc_sample_level(mlmc_ctx* ctx, int level, uint64_t seed
     return fail(ctx, MLMC_ERR_ARG, "mlmc_sample_level: bad arguments");
   if (!check_ws(ctx, ws, ws_bytes, pair_ws(ctx, level, n).total)) return MLMC_ERR_WORKSPACE;
   if (n == 0) return MLMC_OK;
+  ctx->sync_used = 0;
   return sample_level_into(ctx, level, seed, ids, n, y, y2, t_fine, t_coarse, info, (char*)ws,
-                           (cudaStream_t)stream);
+                           (cudaStream_t)stream, ctx->aux_pub);
 }
 
 extern "C" mlmc_status mlmc_reset(mlmc_ctx* ctx, void* stream) {
@@ -484,18 +517,27 @@ extern "C" mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, d
 }
 
 // --------------------------------------------------------------- whole run
-static size_t run_ws(const mlmc_ctx* c, int batch) {
-  size_t m = 0;
-  for (int l = 0; l < c->cfg.n_levels; ++l) {
-    size_t s = pair_ws(c, l, batch).total;
-    m = s > m ? s : m;
-  }
-  return align256((size_t)batch * 8) + 2 * align256((size_t)batch * c->lv[0].nodes * 8) + m;
+// mlmc_run workspace: per level, ids, y, y2 and a pair workspace for
+// min(batch, N_l) pairs, so that all levels can run concurrently.
+static size_t level_run_ws(const mlmc_ctx* c, int l, int nb) {
+  return align256((size_t)nb * 8) + 2 * align256((size_t)nb * c->lv[0].nodes * 8) +
+         pair_ws(c, l, nb).total;
 }
 
-extern "C" mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, int batch, size_t* bytes) {
-  if (!ctx || !bytes || batch < 1 || batch > 65535) return MLMC_ERR_ARG;
-  *bytes = run_ws(ctx, batch);
+static int level_batch(int64_t N, int batch) { return (int)(N < batch ? (N > 0 ? N : 1) : batch); }
+
+static size_t run_ws(const mlmc_ctx* c, const int64_t* N_l, int batch) {
+  size_t s = 0;
+  for (int l = 0; l < c->cfg.n_levels; ++l) s += level_run_ws(c, l, level_batch(N_l[l], batch));
+  return s;
+}
+
+extern "C" mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, const int64_t* N_l, int batch,
+                                                size_t* bytes) {
+  if (!ctx || !bytes || !N_l || batch < 1 || batch > 65535) return MLMC_ERR_ARG;
+  for (int l = 0; l < ctx->cfg.n_levels; ++l)
+    if (N_l[l] < 0) return MLMC_ERR_ARG;
+  *bytes = run_ws(ctx, N_l, batch);
   return MLMC_OK;
 }
 
@@ -507,39 +549,48 @@ extern "C" mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed
   int L = ctx->cfg.n_levels;
   for (int l = 0; l < L; ++l)
     if (N_l[l] < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_run: negative sample count");
-  if (!check_ws(ctx, ws, ws_bytes, run_ws(ctx, batch))) return MLMC_ERR_WORKSPACE;
+  if (!check_ws(ctx, ws, ws_bytes, run_ws(ctx, N_l, batch))) return MLMC_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
-  char* p = (char*)ws;
-  uint64_t* ids = (uint64_t*)p; p += align256((size_t)batch * 8);
-  double* y = (double*)p; p += align256((size_t)batch * ctx->lv[0].nodes * 8);
-  double* y2 = (double*)p; p += align256((size_t)batch * ctx->lv[0].nodes * 8);
   mlmc_status r = mlmc_reset(ctx, stream);
   if (r != MLMC_OK) return r;
   ctx->prof = true;
   ctx->ev_used = 0;
+  ctx->sync_used = 0;
   ctx->launches = 0;
   struct ProfOff { mlmc_ctx* c; ~ProfOff() { c->prof = false; } } prof_off{ctx};
-  cudaEvent_t ev[MLMC_MAX_LEVELS + 1];
-  for (int l = 0; l <= L; ++l) CK(ctx, cudaEventCreate(&ev[l]));
+  cudaEvent_t ev[2 * MLMC_MAX_LEVELS];
+  for (int l = 0; l < 2 * L; ++l) CK(ctx, cudaEventCreate(&ev[l]));
+  struct EvFree { cudaEvent_t* e; int n; ~EvFree() { for (int i = 0; i < n; ++i) cudaEventDestroy(e[i]); } }
+      ev_free{ev, 2 * L};
+  // every level runs on its own pair of streams, concurrently with the others
+  char* p = (char*)ws;
   for (int l = 0; l < L; ++l) {
-    CK(ctx, cudaEventRecord(ev[l], st));
-    for (int64_t first = 0; first < N_l[l]; first += batch) {
-      int nb = (int)((N_l[l] - first) < batch ? (N_l[l] - first) : batch);
-      CK(ctx, launch_iota((uint64_t)first, nb, ids, st));
+    cudaStream_t sf = ctx->lvl_stream[2 * l], sc = ctx->lvl_stream[2 * l + 1];
+    const int nbl = level_batch(N_l[l], batch);
+    char* q = p;
+    uint64_t* ids = (uint64_t*)q; q += align256((size_t)nbl * 8);
+    double* y = (double*)q; q += align256((size_t)nbl * ctx->lv[0].nodes * 8);
+    double* y2 = (double*)q; q += align256((size_t)nbl * ctx->lv[0].nodes * 8);
+    p += level_run_ws(ctx, l, nbl);
+    if ((r = order_after(ctx, st, sf)) != MLMC_OK) return r;
+    CK(ctx, cudaEventRecord(ev[2 * l], sf));
+    for (int64_t first = 0; first < N_l[l]; first += nbl) {
+      int nb = (int)((N_l[l] - first) < nbl ? (N_l[l] - first) : nbl);
+      CK(ctx, launch_iota((uint64_t)first, nb, ids, sf));
       ctx->launches += 1;
-      if ((r = sample_level_into(ctx, l, seed, ids, nb, y, y2, nullptr, nullptr, nullptr, p, st)) != MLMC_OK)
+      if ((r = sample_level_into(ctx, l, seed, ids, nb, y, y2, nullptr, nullptr, nullptr, q, sf, sc)) != MLMC_OK)
         return r;
-      if ((r = mlmc_accumulate(ctx, l, y, y2, nb, stream)) != MLMC_OK) return r;
+      if ((r = mlmc_accumulate(ctx, l, y, y2, nb, sf)) != MLMC_OK) return r;
     }
+    CK(ctx, cudaEventRecord(ev[2 * l + 1], sf));
+    if ((r = order_after(ctx, sf, st)) != MLMC_OK) return r;
   }
-  CK(ctx, cudaEventRecord(ev[L], st));
   if ((r = mlmc_estimate(ctx, mean, var, nullptr, nullptr, V_l, nullptr, rmse, stream)) != MLMC_OK) return r;
   for (int l = 0; l < L; ++l) {
     float ms = 0.f;
-    CK(ctx, cudaEventElapsedTime(&ms, ev[l], ev[l + 1]));
+    CK(ctx, cudaEventElapsedTime(&ms, ev[2 * l], ev[2 * l + 1]));
     if (C_l) C_l[l] = N_l[l] > 0 ? ms * 1e-3 / (double)N_l[l] : 0.0;
   }
-  for (int l = 0; l <= L; ++l) cudaEventDestroy(ev[l]);
   unsigned long long cnt[N_COUNTERS];
   CK(ctx, cudaMemcpy(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
   if (stats) {
@@ -557,6 +608,7 @@ extern "C" mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed
     stats[5] = (double)cnt[4];
     stats[6] = (double)cnt[0];
     stats[7] = (double)ctx->launches;
+    stats[8] = (double)cnt[5];
   }
   if (cnt[0]) {
     char b[96];

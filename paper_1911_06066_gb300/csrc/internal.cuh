@@ -106,8 +106,9 @@ cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const S
                                  mlmc_sample_info* info, unsigned long long* counters,
                                  cudaStream_t st);
 // counters (device, may be NULL): [0] non-converged solves, [1] CG iterations x
-// nodes, [2] Newton iterations x nodes, [3] CG truncations, [4] halvings.
-constexpr int N_COUNTERS = 5;
+// nodes, [2] Newton iterations x nodes, [3] CG truncations, [4] halvings,
+// [5] CG iterations x nodes run in FP64 (the others run in FP32).
+constexpr int N_COUNTERS = 6;
 cudaError_t launch_slab_residual(const LevelDesc& lv, const Physics& ph, const double* coef64,
                                  const double* slab, int n, double* F, double* res_max,
                                  cudaStream_t st);

@@ -264,6 +264,7 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
     atomicAdd(counters + 2, (unsigned long long)newton_total * (unsigned long long)N);
     atomicAdd(counters + 3, (unsigned long long)trunc_total);
     atomicAdd(counters + 4, (unsigned long long)halvings);
+    if (sizeof(KR) == 8) atomicAdd(counters + 5, (unsigned long long)cg_total * (unsigned long long)N);
   }
   if (info && threadIdx.x == 0) {
     mlmc_sample_info o;

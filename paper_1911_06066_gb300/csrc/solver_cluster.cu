@@ -488,6 +488,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       atomicAdd(counters + 2, (unsigned long long)newton_total * (unsigned long long)N);
       atomicAdd(counters + 3, (unsigned long long)trunc_total);
       atomicAdd(counters + 4, (unsigned long long)halvings);
+      if (sizeof(KR) == 8) atomicAdd(counters + 5, (unsigned long long)cg_total * (unsigned long long)N);
     }
     if (info) {
       mlmc_sample_info o;
