@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=None, metavar="LEVEL",
+                    help="run one small solve of LEVEL (2 samples, after one warm-up solve) for "
+                         "an ncu capture of the solve kernel, instead of the benchmark")
     return ap.parse_args()
 
 
@@ -271,11 +274,33 @@ def run_ours(args, w):
     print(json.dumps(out))
 
 
+def run_profile_case(args, w):
+    """Two samples of one level of the benchmark workload through mlmc_solve:
+    launch 1 is a warm-up, launch 2 the one to capture (ncu -s 1 -c 1)."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_1911_06066_gb300 import binding as B
+    prec = B.MLMC_PREC_MIXED if args.precision == "mixed" else B.MLMC_PREC_FP64
+    ctx = B.Context(B.make_config(w, prec))
+    level = args.profile_case
+    Z = ctx.kl_field(level, ctx.xi(0, level, torch.arange(2)))
+    ctx.solve(level, Z[:1])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, info = ctx.solve(level, Z)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": level, "precision": args.precision, "samples": 2,
+                      "seconds": time.perf_counter() - t0, "info": B.info_dicts(info)}))
+
+
 def main():
     args = parse()
     from paper_1911_06066_gb300 import workloads as W
     w = W.MLMC2D_3LVL
-    if args.impl == "reference":
+    if args.profile_case is not None:
+        run_profile_case(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_ours(args, w)
