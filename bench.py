@@ -20,6 +20,7 @@ oracle on this host's cores on a bounded sample of the same workload.
 import argparse
 import concurrent.futures
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-eps run and the serving run (reported beside the step time)")
     ap.add_argument("--profile-case", type=int, default=None, metavar="LEVEL",
                     help="run one small solve of LEVEL (2 samples, after one warm-up solve) for "
                          "an ncu capture of the solve kernel, instead of the benchmark")
@@ -230,6 +233,10 @@ def run_ours(args, w):
     torch.cuda.synchronize()
     clk = clocks.stop()
 
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = run_extras(w, B, prec, seed)
+
     ms = dev_ms / args.steps
     e2e_s = wall_s / args.steps
     if world > 1:
@@ -271,7 +278,74 @@ def run_ours(args, w):
         "clocks": clk,
         "cpu_baseline": cpu,
     }
+    out.update(extras)
     print(json.dumps(out))
+
+
+def run_extras(w, B, prec, seed):
+    """Two measurements beside the step time, on the same workload.
+
+    time_to_eps: the adaptive driver (mlmc_run_to_rmse) from pilot counts to a
+    sampling error of eps / sqrt(2), eps = 1e-3 T; wall time of the call.  The
+    bias of this fixed 3-level hierarchy is reported; it exceeds eps, so only
+    the sampling part of the RMSE is driven to the target.  Beside it, the
+    plain FP64 form (block-per-sample kernel, one sample per launch) is
+    timed on a few pairs per level and its time for the same N_l is
+    extrapolated from those per-pair costs.
+
+    serving: an open-loop Poisson stream of level-pair requests at 2000/s with
+    per-request seeds and stimulus centres uniform in [0, 0.2]^2, the levels
+    mixed in the proportions of the adaptive N_l, through the request server.
+    """
+    import numpy as np
+    import torch
+    from paper_1911_06066_gb300 import serving as S
+
+    eps = 1e-3 * w["T"]
+    ctx = B.Context(B.make_config(w, prec))
+    ctx.run([64, 16, 4], seed=seed + 100, batch=64)          # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = ctx.run_to_rmse(eps, [64, 16, 4], max_rounds=8, max_per_level=1 << 20, seed=seed + 200,
+                          batch=512)
+    t_eps = time.perf_counter() - t0
+    N = res["N_l"]
+    stat = float(np.sqrt(np.sum(res["V_l"] / N)))
+    # the plain FP64 one-sample-per-launch form: per-pair cost on a few pairs
+    plain = B.Context(B.make_config(w, B.MLMC_PREC_FP64, solver=B.MLMC_SOLVER_BLOCK))
+    plain.run([1, 1, 1], seed=seed + 300, batch=1)
+    per = []
+    for l, k in enumerate([8, 4, 2]):
+        cnt = [0] * w["levels"]
+        cnt[l] = k
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        plain.reset()
+        plain.run_more([0] * w["levels"], cnt, seed=seed + 400, batch=1)
+        per.append((time.perf_counter() - t1) / k)
+    plain_s = float(np.sum(np.asarray(per) * N))
+    tte = {"eps": eps, "target_sampling_rmse": eps / math.sqrt(2.0), "seconds": t_eps,
+           "N_l": N.tolist(), "V_l": res["V_l"].tolist(), "C_l": res["C_l"].tolist(),
+           "sampling_rmse": stat, "bias": res["bias"], "rmse": res["rmse"],
+           "plain_fp64_one_sample_per_launch": {
+               "seconds_per_pair": per, "seconds_for_same_N_l": plain_s,
+               "how": "8/4/2 pairs per level timed, x N_l (extrapolated)"},
+           "speedup_vs_plain": plain_s / t_eps if t_eps > 0 else None}
+    del ctx, plain
+    # serving
+    mix = N / N.sum()
+    srv_ctx = B.Context(B.make_config(w, prec))
+    srv = B.Server(srv_ctx, max_batch=256, slots=6, mem_budget=8 << 30, max_wait_s=0.005)
+    sched = S.poisson_schedule(2000.0, 2000, mix, rng_seed=seed, per_request_seed=True,
+                               stim_box=(0.0, 0.2))
+    rep = S.run_open_loop(srv, sched, timeout=600)
+    srv.close()
+    serving = {k: rep[k] for k in ("offered_rate", "completed", "seconds", "throughput", "p50_ms",
+                                   "p99_ms", "max_queue", "batches", "arena_peak_bytes", "failed")}
+    serving.update({"rate": 2000.0, "requests": 2000, "level_mix": mix.tolist(),
+                    "variant": "per-request seeds, stimulus centre ~ U[0,0.2]^2",
+                    "max_batch": 256, "slots": 6})
+    return {"time_to_eps": tte, "serving": serving}
 
 
 def run_profile_case(args, w):

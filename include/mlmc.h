@@ -194,27 +194,183 @@ mlmc_status mlmc_reset(mlmc_ctx* ctx, void* stream);
 mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean_l,
                           double* var_l, double* V_l, int64_t* N_l, double* rmse, void* stream);
 
+/* Autotuner for the solve kernel's layout on one level (the paper has no
+ * counterpart; its solver runs on CPU clusters).  Layout codes: -1 the
+ * block-per-sample kernel (global-memory vectors, one CTA per sample); 1, 2,
+ * 4, 8, 16 a thread-block cluster of that many CTAs per sample with every
+ * vector in shared memory (each CTA a band of whole rows; only where a band
+ * fits); 100 + C (C = 1, 2, 4, 8, 16) a cluster of C CTAs per sample with the
+ * vectors in global memory (each CTA a contiguous node range); 0 automatic:
+ * the smallest shared-memory cluster that holds a sample, else global-memory
+ * clusters of up to 16 CTAs.  Each candidate (the block kernel only with
+ * solver = MLMC_SOLVER_AUTO) solves the same n samples (ids device [n], drawn
+ * with `seed`) once and is timed with CUDA events; the fastest becomes the
+ * level's layout for every later solve of this context.
+ * ws: mlmc_workspace_bytes(ctx, level, n).  Outputs (host, may be NULL): best
+ * (its code) and ms [MLMC_TUNE_CANDIDATES] in the order -1, 1, 2, 4, 8, 16,
+ * 101, 102, 104, 108, 116 (-1 where a candidate was not run).  Synchronises
+ * the stream.  A forced cfg.cluster_size still wins over the tuned value. */
+#define MLMC_TUNE_CANDIDATES 11
+mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* ids, int n,
+                          void* ws, size_t ws_bytes, int* best, float* ms, void* stream);
+/* The layout code used for a level, and a way to set it without tuning (e.g.
+ * from a stored tuning result).  A shared-memory cluster size whose band does
+ * not fit falls back to the automatic choice. */
+mlmc_status mlmc_get_layout(const mlmc_ctx* ctx, int level, int* layout);
+mlmc_status mlmc_set_layout(mlmc_ctx* ctx, int level, int layout);
+
 /* Whole MLMC run with fixed sample counts (host N_l[n_levels]): for each level
  * l, sample ids 0..N_l-1 in batches of at most `batch` pairs, mlmc_sample_level
  * + mlmc_accumulate; then mlmc_estimate into the host outputs (as above;
- * synchronises the stream).  Levels run concurrently on streams owned by the
- * context (ordered after the work already on `stream`; `stream` waits for
- * them); within a level the fine and coarse solves of a batch run
- * concurrently.  ws: mlmc_run_workspace_bytes(ctx, N_l, batch) bytes.
- * C_l (host [n_levels], may be NULL): wall time of each level's work divided
- * by N_l (levels overlap, so this is not an exclusive cost).
+ * synchronises the stream).  Resets the running estimates first.  Levels run
+ * concurrently on streams owned by the context (ordered after the work already
+ * on `stream`; `stream` waits for them); within a level the fine and coarse
+ * solves of a batch run concurrently.  ws: mlmc_run_workspace_bytes(ctx, N_l,
+ * batch) bytes.
+ * C_l (host [n_levels], may be NULL): the cost C_l of Sec. 3 per pair of level
+ * l, in seconds: device time of the solve-kernel launches of its fine and
+ * coarse solves (CUDA events around each launch, summed) divided by N_l.
+ * Levels and solves overlap on the device, so this is the cost of a pair
+ * under the same sharing, not an exclusive one.
  * stats (host [9], may be NULL): device ms spent in the per-sample solve
  * kernel (CUDA events around its launches, summed), its launch count, CG and
  * Newton iterations summed over samples and weighted by the nodes of their
  * grid, CG truncations, line-search halvings, non-converged solves, the total
- * number of kernels launched, and the node-weighted CG iterations run in FP64.  Returns MLMC_ERR_NOT_CONVERGED (outputs still
- * written) if any solve failed. */
+ * number of kernels launched, and the node-weighted CG iterations run in
+ * FP64.  Returns MLMC_ERR_NOT_CONVERGED (outputs still written) if any solve
+ * failed. */
 mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed, int batch, void* ws,
                      size_t ws_bytes, double* mean, double* var, double* V_l, double* C_l,
                      double* rmse, double* stats, void* stream);
-/* Workspace bytes for mlmc_run with the given counts (host N_l) and batch. */
+/* Workspace bytes for mlmc_run with the given counts (host N_l) and batch;
+ * also for mlmc_run_more with N_l = its count. */
 mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, const int64_t* N_l, int batch,
                                      size_t* bytes);
+
+/* Incremental run: adds count[l] level-l pairs with sample ids first_id[l] ..
+ * first_id[l]+count[l]-1 (host arrays) to the running estimates, without a
+ * reset, in the same concurrent schedule as mlmc_run.  Because every sample's
+ * random input is a function of (seed, level, id) alone, splitting ids
+ * 0..N-1 over several calls -- or several contexts, on several devices, whose
+ * states are then merged with mlmc_merge_states -- gives the sample set of
+ * one mlmc_run with N_l = N; the merged moments equal it up to the rounding
+ * order of the accumulation.  solve_seconds (host [n_levels], may be NULL):
+ * each level's summed solve-kernel device time.  Synchronises the stream.
+ * ws: mlmc_run_workspace_bytes(ctx, count, batch).  Returns
+ * MLMC_ERR_NOT_CONVERGED if any solve of this call failed. */
+mlmc_status mlmc_run_more(mlmc_ctx* ctx, const int64_t* first_id, const int64_t* count,
+                          uint64_t seed, int batch, void* ws, size_t ws_bytes,
+                          double* solve_seconds, void* stream);
+
+/* Adaptive MLMC with a fixed hierarchy (the sample allocation of Sec. 3):
+ * runs the pilot counts N_pilot[l] (>= 1 each), then up to max_rounds times
+ * estimates V_l (lumped-mass-weighted variance of Y_l) and the cost C_l per
+ * pair (solve-kernel seconds, as for mlmc_run) and raises every level to
+ *   N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)),
+ * capped at max_per_level, running only the new ids.  This is the allocation
+ * that makes the sampling error sum_l V_l / N_l at most eps^2 / 2 at least
+ * total cost.  Stops when no level needs more samples.  Resets the running
+ * estimates first.  Outputs (host): N_l [n_levels] samples used, mean, var
+ * [nodes_0] (may be NULL), V_l, C_l [n_levels] (may be NULL), rmse (as
+ * mlmc_estimate, sampling error plus squared bias) and bias (the weighted norm
+ * of the finest level's mean correction, an estimate of the discretisation
+ * bias; 0 for one level) (may be NULL).  ws:
+ * mlmc_run_workspace_bytes(ctx, {batch, ..., batch}, batch) bytes. */
+mlmc_status mlmc_run_to_rmse(mlmc_ctx* ctx, double eps, const int64_t* N_pilot, int max_rounds,
+                             int64_t max_per_level, uint64_t seed, int batch, void* ws,
+                             size_t ws_bytes, int64_t* N_l, double* mean, double* var,
+                             double* V_l, double* C_l, double* rmse, double* bias, void* stream);
+
+/* Accumulator state (checkpoint / resume, and the cross-device merge).  The
+ * state of a context is, per level l, the sample count N_l and per coarsest-
+ * grid node the running mean and sum of squared deviations of the injected
+ * difference Y_l and the running mean of t_l^2 - t_{l-1}^2: host arrays
+ * N_l [n_levels] and mean_l, m2_l, mean2_l [n_levels][nodes_0] (row l at
+ * offset l * nodes_0).  mlmc_get_state copies it out (any pointer may be
+ * NULL; synchronises the stream); mlmc_set_state replaces it (all required).
+ */
+mlmc_status mlmc_get_state(mlmc_ctx* ctx, int64_t* N_l, double* mean_l, double* m2_l,
+                           double* mean2_l, void* stream);
+mlmc_status mlmc_set_state(mlmc_ctx* ctx, const int64_t* N_l, const double* mean_l,
+                           const double* m2_l, const double* mean2_l, void* stream);
+/* Host-only merge of state b into state a (same layout as above): for every
+ * level the pairwise update of Chan, Golub and LeVeque (1979) for count,
+ * mean and sum of squared deviations, and the count-weighted mean of mean2.
+ * Runs on the CPU, needs no device or context; the single exchange step of a
+ * multi-device run.  MLMC_ERR_ARG on NULL pointers or negative counts. */
+mlmc_status mlmc_merge_states(int levels, int64_t nodes0, int64_t* N_a, double* mean_a,
+                              double* m2_a, double* mean2_a, const int64_t* N_b,
+                              const double* mean_b, const double* m2_b, const double* mean2_b);
+
+/* ------------------------------------------------------------------ serving
+ * Request server on one context (the paper has no counterpart; it is the
+ * serving form of the method: MLMC sample requests arrive over time and the
+ * running estimate is updated as they finish).  A request is one level pair
+ * (level, seed, sample id) with an optional stimulus centre.  A native
+ * scheduler thread admits queued requests as batches of one level whenever a
+ * slot (a pair of streams) is free and a device arena of mem_budget bytes,
+ * allocated once at creation, has room for the batch (a batch that does not
+ * fit is halved until it does: memory-based admission).  Batches of different
+ * levels run concurrently.  Finished batches are merged into the context's
+ * running estimates (mlmc_accumulate order: completion order) and their
+ * results are queued for mlmc_server_poll.  A request's result depends only on
+ * the request, not on what else is in flight.  While a server exists, the
+ * context must not be used directly.  Times are seconds on the server's
+ * monotonic clock (0 at creation). */
+typedef struct mlmc_server mlmc_server;
+
+typedef struct {
+  int max_batch;      /* most requests of one level in one launch, 1..65535 */
+  int slots;          /* batches in flight at once, 1..16 */
+  size_t mem_budget;  /* device bytes for in-flight batches (the arena) */
+  int keep_maps;      /* nonzero: results carry the fine activation map */
+  double max_wait_s;  /* hold a partial batch this long while the device is busy */
+} mlmc_server_config;
+
+typedef struct {
+  int64_t tag;        /* caller's identifier, returned in the result */
+  int level;          /* level pair, 0..n_levels-1 */
+  int pad;
+  uint64_t seed;      /* xi seed of this request (Philox key) */
+  uint64_t sample_id; /* xi counter of this request */
+  double stim_c[3];   /* stimulus centre; NaN in stim_c[0]: the configuration's */
+} mlmc_request;
+
+typedef struct {
+  int64_t tag;
+  int level;
+  int status;         /* MLMC_OK, or the status of a failed solve */
+  int newton_iters;   /* summed over the pair's solves */
+  int cg_iters;
+  double t_submit, t_admit, t_done;
+} mlmc_result;
+
+/* Creates the server and starts its scheduler thread.  MLMC_ERR_WORKSPACE if
+ * mem_budget cannot hold one request of the largest level. */
+mlmc_status mlmc_server_create(mlmc_ctx* ctx, const mlmc_server_config* cfg, mlmc_server** out);
+/* Queues n requests (host array, copied); thread-safe, does not block on the
+ * device.  MLMC_ERR_ARG for a level out of range (nothing queued). */
+mlmc_status mlmc_server_submit(mlmc_server* s, const mlmc_request* reqs, int n);
+/* Takes up to max finished results (host out[max]); waits up to timeout_s for
+ * the first.  y (host [max][nodes_0] or NULL) receives each request's Y_l on
+ * the coarsest grid; maps (host [max][map_stride] or NULL, keep_maps only) its
+ * fine activation map (nodes of its level).  Thread-safe. */
+mlmc_status mlmc_server_poll(mlmc_server* s, mlmc_result* out, int max, int* count, double* y,
+                             double* maps, int64_t map_stride, double timeout_s);
+/* Waits until every submitted request has finished (MLMC_ERR_TIMEOUT after
+ * timeout_s). */
+mlmc_status mlmc_server_drain(mlmc_server* s, double timeout_s);
+/* stats (host [8]): submitted, queued, in flight, completed, batches launched,
+ * largest queue length seen, peak arena bytes, sticky error status. */
+mlmc_status mlmc_server_stats(mlmc_server* s, int64_t* stats);
+mlmc_status mlmc_server_clock(mlmc_server* s, double* now);
+/* The running MLMC estimate over the finished requests (as mlmc_estimate;
+ * host outputs, any may be NULL; bias as in mlmc_run_to_rmse). */
+mlmc_status mlmc_server_estimate(mlmc_server* s, double* mean, double* var, double* V_l,
+                                 int64_t* N_l, double* rmse, double* bias);
+const char* mlmc_server_error(mlmc_server* s);
+/* Stops admitting, waits for the batches in flight, frees everything. */
+void mlmc_server_destroy(mlmc_server* s);
 
 /* Allocation-free variant of mlmc_solve (the paper has no counterpart; this is
  * a deployment aid).  For callers that may not allocate device memory -- for

@@ -44,6 +44,22 @@ class mlmc_sample_info(C.Structure):
 
 INFO_FIELDS = [f[0] for f in mlmc_sample_info._fields_ if f[0] != "pad"]
 
+
+class mlmc_server_config(C.Structure):
+    _fields_ = [("max_batch", C.c_int), ("slots", C.c_int), ("mem_budget", C.c_size_t),
+                ("keep_maps", C.c_int), ("max_wait_s", C.c_double)]
+
+
+class mlmc_request(C.Structure):
+    _fields_ = [("tag", C.c_int64), ("level", C.c_int), ("pad", C.c_int), ("seed", C.c_uint64),
+                ("sample_id", C.c_uint64), ("stim_c", C.c_double * 3)]
+
+
+class mlmc_result(C.Structure):
+    _fields_ = [("tag", C.c_int64), ("level", C.c_int), ("status", C.c_int),
+                ("newton_iters", C.c_int), ("cg_iters", C.c_int), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double)]
+
 _lib = None
 
 
@@ -80,6 +96,24 @@ def lib():
             "mlmc_estimate": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], ip),
             "mlmc_run": ([vp, vp, u64, ip, vp, sz, vp, vp, vp, vp, vp, vp, vp], ip),
             "mlmc_run_workspace_bytes": ([vp, vp, ip, C.POINTER(sz)], ip),
+            "mlmc_run_more": ([vp, vp, vp, u64, ip, vp, sz, vp, vp], ip),
+            "mlmc_run_to_rmse": ([vp, C.c_double, vp, ip, i64, u64, ip, vp, sz, vp, vp, vp, vp, vp,
+                                  vp, vp, vp], ip),
+            "mlmc_get_state": ([vp, vp, vp, vp, vp, vp], ip),
+            "mlmc_set_state": ([vp, vp, vp, vp, vp, vp], ip),
+            "mlmc_merge_states": ([ip, i64, vp, vp, vp, vp, vp, vp, vp, vp], ip),
+            "mlmc_autotune": ([vp, ip, u64, vp, ip, vp, sz, C.POINTER(ip), vp, vp], ip),
+            "mlmc_get_layout": ([vp, ip, C.POINTER(ip)], ip),
+            "mlmc_set_layout": ([vp, ip, ip], ip),
+            "mlmc_server_create": ([vp, C.POINTER(mlmc_server_config), C.POINTER(vp)], ip),
+            "mlmc_server_submit": ([vp, vp, ip], ip),
+            "mlmc_server_poll": ([vp, vp, ip, C.POINTER(ip), vp, vp, i64, C.c_double], ip),
+            "mlmc_server_drain": ([vp, C.c_double], ip),
+            "mlmc_server_stats": ([vp, vp], ip),
+            "mlmc_server_clock": ([vp, C.POINTER(C.c_double)], ip),
+            "mlmc_server_estimate": ([vp, vp, vp, vp, vp, vp, vp], ip),
+            "mlmc_server_error": ([vp], C.c_char_p),
+            "mlmc_server_destroy": ([vp], None),
             "mlmc_solve_noalloc": ([C.POINTER(mlmc_config), ip, vp, ip, vp, vp, vp], ip),
         }
         for name, (args, res) in sig.items():
@@ -95,7 +129,58 @@ def exported_symbols():
     return ["mlmc_create", "mlmc_destroy", "mlmc_last_error", "mlmc_level_info",
             "mlmc_workspace_bytes", "mlmc_xi", "mlmc_kl_field", "mlmc_solve", "mlmc_slab_residual",
             "mlmc_activation", "mlmc_sample_level", "mlmc_accumulate", "mlmc_reset",
-            "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_solve_noalloc"]
+            "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_run_more",
+            "mlmc_run_to_rmse", "mlmc_get_state", "mlmc_set_state", "mlmc_merge_states",
+            "mlmc_autotune", "mlmc_get_layout", "mlmc_set_layout", "mlmc_server_create",
+            "mlmc_server_submit", "mlmc_server_poll", "mlmc_server_drain", "mlmc_server_stats",
+            "mlmc_server_clock", "mlmc_server_estimate", "mlmc_server_error",
+            "mlmc_server_destroy", "mlmc_solve_noalloc"]
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class State:
+    """Host copy of a context's accumulator state: per level the sample count
+    ``N`` [L], running mean ``mean`` [L][nodes_0] and sum of squared
+    deviations ``m2`` of the injected difference Y_l, and the running mean
+    ``mean2`` of t_l^2 - t_{l-1}^2."""
+
+    def __init__(self, N, mean, m2, mean2):
+        self.N = np.ascontiguousarray(N, np.int64)
+        self.mean = np.ascontiguousarray(mean, np.float64)
+        self.m2 = np.ascontiguousarray(m2, np.float64)
+        self.mean2 = np.ascontiguousarray(mean2, np.float64)
+
+    @classmethod
+    def empty(cls, levels, nodes0):
+        z = np.zeros((levels, nodes0))
+        return cls(np.zeros(levels, np.int64), z, z.copy(), z.copy())
+
+    def as_array(self):
+        """One flat float64 vector (counts first) for a collective or a file."""
+        return np.concatenate([self.N.astype(np.float64), self.mean.ravel(), self.m2.ravel(),
+                               self.mean2.ravel()])
+
+    @classmethod
+    def from_array(cls, a, levels, nodes0):
+        a = np.asarray(a, np.float64)
+        k = levels * nodes0
+        N = np.rint(a[:levels]).astype(np.int64)
+        r = a[levels:]
+        return cls(N, r[:k].reshape(levels, nodes0), r[k:2 * k].reshape(levels, nodes0),
+                   r[2 * k:3 * k].reshape(levels, nodes0))
+
+    def merge(self, other):
+        """In place: self <- self merged with other (mlmc_merge_states, on the CPU)."""
+        L, n0 = self.mean.shape
+        st = lib().mlmc_merge_states(L, n0, _dp(self.N), _dp(self.mean), _dp(self.m2),
+                                     _dp(self.mean2), _dp(other.N), _dp(other.mean), _dp(other.m2),
+                                     _dp(other.mean2))
+        if st != MLMC_OK:
+            raise MLMCError(st, "mlmc_merge_states")
+        return self
 
 
 def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=500, lin_rtol=1e-12,
@@ -293,6 +378,168 @@ class Context:
                 "halvings", "failed", "launches", "cg64_node_iters")
         return dict(mean=mean, var=var, V_l=V, C_l=Cl, rmse=rmse.value, N_l=Nh,
                     stats=dict(zip(keys, stats.tolist())))
+
+    def run_more(self, first_id, count, seed=0, batch=None, stream=None):
+        """Adds pairs with ids first_id[l] .. first_id[l]+count[l]-1 per level to
+        the running estimates (no reset).  Returns each level's solve seconds."""
+        L = self.cfg.n_levels
+        F = np.ascontiguousarray(first_id, np.int64)
+        Nc = np.ascontiguousarray(count, np.int64)
+        batch = batch or int(max(1, Nc.max()))
+        secs = np.zeros(L)
+        nb = self.run_workspace_bytes(Nc, batch)
+        ws = self.workspace(nb, key="run")
+        self._check(lib().mlmc_run_more(self.h, _dp(F), _dp(Nc), seed, batch, _p(ws), ws.numel(),
+                                        _dp(secs), _stream(stream)))
+        return secs
+
+    def run_to_rmse(self, eps, N_pilot, max_rounds=8, max_per_level=1 << 20, seed=0, batch=64,
+                    stream=None):
+        """Adaptive MLMC to sampling error eps / sqrt(2) (mlmc_run_to_rmse)."""
+        L = self.cfg.n_levels
+        n0, _, _ = self.level_info(0)
+        P = np.ascontiguousarray(N_pilot, np.int64)
+        N = np.zeros(L, np.int64)
+        mean, var, V, Cl = np.zeros(n0), np.zeros(n0), np.zeros(L), np.zeros(L)
+        rmse, bias = C.c_double(), C.c_double()
+        nb = self.run_workspace_bytes(np.full(L, batch, np.int64), batch)
+        ws = self.workspace(nb, key="run")
+        self._check(lib().mlmc_run_to_rmse(self.h, eps, _dp(P), max_rounds, max_per_level, seed,
+                                           batch, _p(ws), ws.numel(), _dp(N), _dp(mean), _dp(var),
+                                           _dp(V), _dp(Cl), C.byref(rmse), C.byref(bias),
+                                           _stream(stream)))
+        return dict(N_l=N, mean=mean, var=var, V_l=V, C_l=Cl, rmse=rmse.value, bias=bias.value)
+
+    def autotune(self, level, n, seed=0, first_id=0, stream=None):
+        """Times every feasible solve layout of ``level`` on n samples and keeps
+        the fastest; returns (layout, {layout: ms})."""
+        import torch
+        ids = torch.arange(first_id, first_id + n, dtype=torch.int64, device="cuda")
+        ws = self.workspace(self.workspace_bytes(level, n), key="tune")
+        best = C.c_int()
+        ms = np.zeros(11, np.float32)
+        self._check(lib().mlmc_autotune(self.h, level, seed, _p(ids), n, _p(ws), ws.numel(),
+                                        C.byref(best), _dp(ms), _stream(stream)))
+        names = (-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116)
+        return best.value, {k: float(v) for k, v in zip(names, ms) if v >= 0}
+
+    def layout(self, level):
+        c = C.c_int()
+        self._check(lib().mlmc_get_layout(self.h, level, C.byref(c)))
+        return c.value
+
+    def set_layout(self, level, layout):
+        self._check(lib().mlmc_set_layout(self.h, level, layout))
+
+    def get_state(self, stream=None):
+        L = self.cfg.n_levels
+        n0, _, _ = self.level_info(0)
+        s = State.empty(L, n0)
+        self._check(lib().mlmc_get_state(self.h, _dp(s.N), _dp(s.mean), _dp(s.m2), _dp(s.mean2),
+                                         _stream(stream)))
+        return s
+
+    def set_state(self, s, stream=None):
+        self._check(lib().mlmc_set_state(self.h, _dp(s.N), _dp(s.mean), _dp(s.m2), _dp(s.mean2),
+                                         _stream(stream)))
+
+
+class Server:
+    """A request server on one Context (mlmc_server_*): submit level-pair
+    requests at any time, poll finished results, read the running estimate.
+    The Context must not be used directly while the server exists."""
+
+    def __init__(self, ctx, max_batch=32, slots=4, mem_budget=1 << 30, keep_maps=False,
+                 max_wait_s=0.0):
+        self.ctx = ctx
+        self.cfg = mlmc_server_config(max_batch, slots, mem_budget, int(keep_maps), max_wait_s)
+        h = C.c_void_p()
+        st = lib().mlmc_server_create(ctx.h, C.byref(self.cfg), C.byref(h))
+        if st != MLMC_OK:
+            raise MLMCError(st, lib().mlmc_last_error(ctx.h).decode())
+        self.h = h
+        self.n0 = ctx.level_info(0)[0]
+        self.nL = ctx.level_info(ctx.cfg.n_levels - 1)[0]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mlmc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != MLMC_OK:
+            raise MLMCError(st, lib().mlmc_server_error(self.h).decode())
+
+    @staticmethod
+    def requests(tags, levels, seeds, sample_ids, stim=None):
+        """A ctypes array of requests; stim [n][2 or 3] or None (configured centre)."""
+        n = len(tags)
+        arr = (mlmc_request * n)()
+        for i in range(n):
+            r = arr[i]
+            r.tag, r.level, r.seed, r.sample_id = int(tags[i]), int(levels[i]), int(seeds[i]), \
+                int(sample_ids[i])
+            if stim is None:
+                r.stim_c[0], r.stim_c[1], r.stim_c[2] = float("nan"), 0.0, 0.0
+            else:
+                c = list(stim[i]) + [0.0] * (3 - len(stim[i]))
+                r.stim_c[0], r.stim_c[1], r.stim_c[2] = c[0], c[1], c[2]
+        return arr
+
+    def submit(self, reqs):
+        self._check(lib().mlmc_server_submit(self.h, C.cast(reqs, C.c_void_p), len(reqs)))
+
+    def poll(self, max_results=4096, timeout=0.0, want_y=False, want_maps=False):
+        """Finished results as a list of dicts (with 'y' / 'map' arrays if asked)."""
+        out = (mlmc_result * max_results)()
+        cnt = C.c_int()
+        y = np.zeros((max_results, self.n0)) if want_y else None
+        maps = np.zeros((max_results, self.nL)) if want_maps else None
+        self._check(lib().mlmc_server_poll(self.h, C.cast(out, C.c_void_p), max_results, C.byref(cnt),
+                                           None if y is None else _dp(y),
+                                           None if maps is None else _dp(maps), self.nL, timeout))
+        res = []
+        for i in range(cnt.value):
+            r = out[i]
+            d = dict(tag=r.tag, level=r.level, status=r.status, newton_iters=r.newton_iters,
+                     cg_iters=r.cg_iters, t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done)
+            if y is not None:
+                d["y"] = y[i].copy()
+            if maps is not None:
+                nl = self.ctx.level_info(r.level)[0]
+                d["map"] = maps[i, :nl].copy()
+            res.append(d)
+        return res
+
+    def drain(self, timeout=600.0):
+        self._check(lib().mlmc_server_drain(self.h, timeout))
+
+    def stats(self):
+        a = np.zeros(8, np.int64)
+        self._check(lib().mlmc_server_stats(self.h, _dp(a)))
+        keys = ("submitted", "queued", "inflight", "completed", "batches", "max_queue",
+                "arena_peak_bytes", "error")
+        return dict(zip(keys, a.tolist()))
+
+    def clock(self):
+        t = C.c_double()
+        self._check(lib().mlmc_server_clock(self.h, C.byref(t)))
+        return t.value
+
+    def estimate(self):
+        L = self.ctx.cfg.n_levels
+        mean, var, V = np.zeros(self.n0), np.zeros(self.n0), np.zeros(L)
+        N = np.zeros(L, np.int64)
+        rmse, bias = C.c_double(), C.c_double()
+        self._check(lib().mlmc_server_estimate(self.h, _dp(mean), _dp(var), _dp(V), _dp(N),
+                                               C.byref(rmse), C.byref(bias)))
+        return dict(mean=mean, var=var, V_l=V, N_l=N, rmse=rmse.value, bias=bias.value)
 
 
 def info_dicts(info):

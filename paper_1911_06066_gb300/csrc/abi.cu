@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "internal.cuh"
+#include "ctx.cuh"
 
 namespace mlmc {
 void kl_1d_host(double len, double ell, int n, std::vector<double>& omega, std::vector<double>& lam,
@@ -21,34 +21,6 @@ cudaError_t launch_iota(uint64_t first, int n, uint64_t* ids, cudaStream_t st);
 
 using namespace mlmc;
 
-struct mlmc_ctx {
-  mlmc_config cfg;
-  int device;
-  LevelDesc lv[MLMC_MAX_LEVELS];
-  Physics ph;
-  SolverParams sp;
-  int M;
-  double* d_sqrt_lam = nullptr;
-  int* d_idx = nullptr;
-  double* d_phi[MLMC_MAX_LEVELS][3] = {};
-  double* d_acc = nullptr;        // [3][levels][nodes0]: mean, M2, mean of Y2
-  int64_t* d_N = nullptr;         // [levels]
-  double* d_est = nullptr;        // estimate output
-  unsigned long long* d_cnt = nullptr;  // solver counters (see N_COUNTERS)
-  int64_t N_acc[MLMC_MAX_LEVELS] = {};
-  // streams for concurrent solves: [2l] fine / [2l+1] coarse solves of level
-  // l inside mlmc_run; aux_pub for the coarse solve of mlmc_sample_level
-  cudaStream_t lvl_stream[2 * MLMC_MAX_LEVELS] = {};
-  cudaStream_t aux_pub = nullptr;
-  std::vector<cudaEvent_t> sync_pool;   // ordering-only events
-  size_t sync_used = 0;
-  // launch accounting and solve-kernel timing, active inside mlmc_run
-  bool prof = false;
-  long launches = 0;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  std::string err;
-};
 
 static thread_local std::string g_create_error;
 
@@ -57,23 +29,17 @@ namespace mlmc {
 void set_create_error(const std::string& msg) { g_create_error = msg; }
 }  // namespace mlmc
 
-static mlmc_status fail(mlmc_ctx* ctx, mlmc_status st, const std::string& msg) {
+mlmc_status mlmc::fail(mlmc_ctx* ctx, mlmc_status st, const std::string& msg) {
   if (ctx) ctx->err = msg; else g_create_error = msg;
   return st;
 }
 
-static mlmc_status cuda_fail(mlmc_ctx* ctx, cudaError_t e, const char* where) {
+mlmc_status mlmc::cuda_fail(mlmc_ctx* ctx, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorString(e);
   return fail(ctx, e == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA, m);
 }
 
-#define CK(ctx, expr)                                        \
-  do {                                                       \
-    cudaError_t _e = (expr);                                 \
-    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr); \
-  } while (0)
 
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // --------------------------------------------------------------- workspace
 // FP32 inner solves are used only where the step Jacobian is at most mildly
@@ -106,11 +72,7 @@ static SolveWs solve_ws(const LevelDesc& lv, int n, bool mixed) {
   return w;
 }
 
-struct PairWs {
-  size_t xi, Zf, Zc, tf, tc, info, solve_f, solve_c, total;
-};
-
-static PairWs pair_ws(const mlmc_ctx* c, int level, int n) {
+PairWs mlmc::pair_ws(const mlmc_ctx* c, int level, int n) {
   PairWs w;
   const LevelDesc& lf = c->lv[level];
   size_t off = 0;
@@ -190,6 +152,7 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
     lv.dt = c.T / (double)lv.m;
   }
   Physics& ph = ctx->ph;
+  ph.stim_ps = nullptr;
   ph.c = c.c; ph.a = c.a; ph.s_t = c.s_t; ph.s_l0 = c.s_l0;
   ph.th0 = c.theta0_deg * pi / 180.0;
   ph.th1 = c.theta1_deg * pi / 180.0;
@@ -273,7 +236,7 @@ extern "C" const char* mlmc_last_error(const mlmc_ctx* ctx) {
 
 // Make `waiter` wait for the work enqueued so far on `src` (an ordering-only
 // event from the context's pool).
-static mlmc_status order_after(mlmc_ctx* ctx, cudaStream_t src, cudaStream_t waiter) {
+mlmc_status mlmc::order_after(mlmc_ctx* ctx, cudaStream_t src, cudaStream_t waiter) {
   if (src == waiter) return MLMC_OK;
   if (ctx->sync_used == ctx->sync_pool.size()) {
     cudaEvent_t ev;
@@ -317,7 +280,7 @@ extern "C" mlmc_status mlmc_xi(mlmc_ctx* ctx, uint64_t seed, int level, const ui
   if (!ctx) return MLMC_ERR_ARG;
   if (n < 0 || (n > 0 && (!ids || !xi))) return fail(ctx, MLMC_ERR_ARG, "mlmc_xi: bad arguments");
   if (level < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_xi: negative level");
-  CK(ctx, launch_xi(seed, level, ids, n, ctx->M, xi, (cudaStream_t)stream));
+  CK(ctx, launch_xi(seed, nullptr, level, ids, n, ctx->M, xi, (cudaStream_t)stream));
   return MLMC_OK;
 }
 
@@ -335,19 +298,44 @@ extern "C" mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi,
 
 // Coefficients + sweep for n samples of one level inside an already checked
 // workspace region.
+// The solve layout of a level: false = the block-per-sample kernel, else a
+// cluster plan.  Layout codes (mlmc_set_layout): -1 block kernel, 0 automatic
+// (the smallest shared-memory cluster that holds a sample, else global-memory
+// clusters), 1..16 shared-memory clusters of that size, 100 + C global-memory
+// clusters of C CTAs.
+static bool choose_plan(const mlmc_ctx* ctx, const LevelDesc& lv, bool mixed, int level,
+                        ClusterPlan* plan) {
+  if (ctx->cfg.solver == MLMC_SOLVER_BLOCK) return false;
+  const int want = ctx->cfg.cluster_size ? ctx->cfg.cluster_size : ctx->tuned_C[level];
+  if (want < 0 && ctx->cfg.solver == MLMC_SOLVER_AUTO) return false;
+  if (want > 100) return cluster_plan(lv, mixed, want - 100, plan, true);
+  if (want > 0 && cluster_plan(lv, mixed, want, plan)) return true;
+  if (cluster_plan(lv, mixed, 0, plan)) return true;
+  return cluster_plan(lv, mixed, 0, plan, true);
+}
+
+static bool valid_layout(int C) {
+  const int ok[12] = {-1, 0, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116};
+  for (int v : ok)
+    if (C == v) return true;
+  return false;
+}
+
 static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, double* t_act,
-                              double* slab, mlmc_sample_info* info, char* ws, cudaStream_t st) {
+                              double* slab, mlmc_sample_info* info, char* ws, cudaStream_t st,
+                              const double* stim = nullptr) {
+  Physics ph = ctx->ph;
+  ph.stim_ps = stim;
   const LevelDesc& lv = ctx->lv[level];
   bool mixed = level_mixed(ctx->cfg, lv);
   SolveWs w = solve_ws(lv, n, mixed);
   double* coef64 = (double*)(ws + w.coef64);
   float* coef32 = mixed ? (float*)(ws + w.coef32) : nullptr;
-  CK(ctx, launch_assemble(lv, ctx->ph, Z, n, coef64, coef32, st));
+  CK(ctx, launch_assemble(lv, ph, Z, n, coef64, coef32, st));
   ClusterPlan plan;
-  bool use_cluster = ctx->cfg.solver != MLMC_SOLVER_BLOCK &&
-                     cluster_plan(lv, mixed, ctx->cfg.cluster_size, &plan);
+  const bool use_cluster = choose_plan(ctx, lv, mixed, level, &plan);
   if (ctx->cfg.solver == MLMC_SOLVER_CLUSTER && !use_cluster)
-    return fail(ctx, MLMC_ERR_ARG, "cluster layout requested but a sample of this level does not fit");
+    return fail(ctx, MLMC_ERR_ARG, "cluster layout requested but no cluster plan fits");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ctx->prof) {
     while (ctx->ev_pool.size() < ctx->ev_used + 2) {
@@ -357,16 +345,23 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     }
     e0 = ctx->ev_pool[ctx->ev_used++];
     e1 = ctx->ev_pool[ctx->ev_used++];
+    ctx->ev_level.push_back(ctx->prof_level);
     CK(ctx, cudaEventRecord(e0, st));
   }
   SolverParams sp = ctx->sp;
   sp.lin_rtol = mixed ? fmax(ctx->cfg.lin_rtol, 1e-5) : ctx->cfg.lin_rtol;
   sp.step_max = step_limit(ctx->cfg.c, ctx->cfg.a, lv.dt);
-  if (use_cluster)
-    CK(ctx, launch_solve_cluster(lv, ctx->ph, sp, mixed, plan, n, coef64, coef32, slab, t_act, info,
-                                 ctx->d_cnt, st));
+  if (use_cluster) {
+    ClusterGlobal g;
+    g.u = (double*)(ws + w.ubuf);
+    g.F = (double*)(ws + w.F);
+    g.kr = (void*)(ws + w.kr);
+    g.code = (unsigned*)(ws + w.Ku);
+    CK(ctx, launch_solve_cluster(lv, ph, sp, mixed, plan, n, coef64, coef32, slab, t_act, info,
+                                 ctx->d_cnt, g, st));
+  }
   else
-    CK(ctx, launch_solve(lv, ctx->ph, sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
+    CK(ctx, launch_solve(lv, ph, sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
                          (double*)(ws + w.F), (double*)(ws + w.Ku), (double*)(ws + w.Kd),
                          (void*)(ws + w.kr), t_act, info, ctx->d_cnt, st));
   if (ctx->prof) CK(ctx, cudaEventRecord(e1, st));
@@ -385,6 +380,92 @@ extern "C" mlmc_status mlmc_solve(mlmc_ctx* ctx, int level, const double* Z, int
   if (!check_ws(ctx, ws, ws_bytes, need)) return MLMC_ERR_WORKSPACE;
   if (n == 0) return MLMC_OK;
   return solve_into(ctx, level, Z, n, t_act, slab, info, (char*)ws, (cudaStream_t)stream);
+}
+
+// Autotuner: the solve kernel's layout for one level (block-per-sample, or a
+// cluster of C = 1..16 CTAs per sample, each with its own band height) is
+// timed on n samples of the level with CUDA events and the fastest is kept.
+extern "C" mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* ids,
+                                     int n, void* ws, size_t ws_bytes, int* best, float* ms,
+                                     void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level)) return MLMC_ERR_ARG;
+  if (n < 1 || n > 65535 || !ids) return fail(ctx, MLMC_ERR_ARG, "mlmc_autotune: bad arguments");
+  if (!check_ws(ctx, ws, ws_bytes, pair_ws(ctx, level, n).total)) return MLMC_ERR_WORKSPACE;
+  const LevelDesc& lv = ctx->lv[level];
+  const bool mixed = level_mixed(ctx->cfg, lv);
+  cudaStream_t st = (cudaStream_t)stream;
+  PairWs w = pair_ws(ctx, level, n);
+  char* p = (char*)ws;
+  double* xi = (double*)(p + w.xi);
+  double* Z = (double*)(p + w.Zf);
+  double* t = (double*)(p + w.tf);
+  mlmc_sample_info* inf = (mlmc_sample_info*)(p + w.info);
+  CK(ctx, launch_xi(seed, nullptr, level, ids, n, ctx->M, xi, st));
+  mlmc_status r;
+  if ((r = mlmc_kl_field(ctx, level, xi, n, Z, st)) != MLMC_OK) return r;
+  // candidates: the block kernel (only when the layout is not forced), shared-
+  // memory clusters of 1..16 CTAs (where a band fits), global-memory clusters
+  const int cand[MLMC_TUNE_CANDIDATES] = {-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116};
+  float t_ms[MLMC_TUNE_CANDIDATES];
+  int choice = 0;
+  float best_ms = 0.f;
+  const int saved = ctx->tuned_C[level];
+  const bool saved_prof = ctx->prof;
+  ctx->prof = false;
+  struct Restore {
+    mlmc_ctx* c; int l; int v; bool pr;
+    ~Restore() { c->tuned_C[l] = v; c->prof = pr; }
+  } restore{ctx, level, saved, saved_prof};
+  cudaEvent_t e[2];
+  CK(ctx, cudaEventCreate(&e[0]));
+  CK(ctx, cudaEventCreate(&e[1]));
+  struct EvFree { cudaEvent_t* e; ~EvFree() { cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); } } ev_free{e};
+  for (int i = 0; i < MLMC_TUNE_CANDIDATES; ++i) {
+    t_ms[i] = -1.f;
+    const int C = cand[i];
+    if (C < 0 && ctx->cfg.solver != MLMC_SOLVER_AUTO) continue;
+    if (C > 0) {
+      ClusterPlan pl;
+      if (ctx->cfg.solver == MLMC_SOLVER_BLOCK) continue;
+      if (!cluster_plan(lv, mixed, C > 100 ? C - 100 : C, &pl, C > 100)) continue;
+      int active = 0;
+      CK(ctx, cluster_max_active(lv, mixed, pl, &active));
+      if (active < 1) continue;
+    } else {
+      CK(ctx, preload_solve(lv, mixed));
+    }
+    ctx->tuned_C[level] = C;
+    const int force = ctx->cfg.cluster_size;
+    ctx->cfg.cluster_size = 0;
+    CK(ctx, cudaEventRecord(e[0], st));
+    r = solve_into(ctx, level, Z, n, t, nullptr, inf, p + w.solve_f, st);
+    ctx->cfg.cluster_size = force;
+    if (r != MLMC_OK) return r;
+    CK(ctx, cudaEventRecord(e[1], st));
+    CK(ctx, cudaEventSynchronize(e[1]));
+    CK(ctx, cudaEventElapsedTime(&t_ms[i], e[0], e[1]));
+    if (best_ms == 0.f || t_ms[i] < best_ms) { best_ms = t_ms[i]; choice = C; }
+  }
+  if (best_ms == 0.f) return fail(ctx, MLMC_ERR_ARG, "mlmc_autotune: no solver layout fits this level");
+  restore.v = choice;
+  if (best) *best = choice;
+  if (ms) memcpy(ms, t_ms, sizeof t_ms);
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_get_layout(const mlmc_ctx* ctx, int level, int* C) {
+  if (!ctx || !C || level < 0 || level >= ctx->cfg.n_levels) return MLMC_ERR_ARG;
+  *C = ctx->cfg.cluster_size ? ctx->cfg.cluster_size : ctx->tuned_C[level];
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_set_layout(mlmc_ctx* ctx, int level, int C) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level) || !valid_layout(C))
+    return fail(ctx, MLMC_ERR_ARG, "mlmc_set_layout: level or layout out of range");
+  ctx->tuned_C[level] = C;
+  return MLMC_OK;
 }
 
 extern "C" mlmc_status mlmc_slab_residual(mlmc_ctx* ctx, int level, const double* Z,
@@ -420,16 +501,17 @@ extern "C" mlmc_status mlmc_activation(mlmc_ctx* ctx, int level, const double* s
 
 // One batch of level-l pairs: xi and both fields on st_f, the fine solve on
 // st_f and the coarse solve concurrently on st_c, then the differences on st_f.
-static mlmc_status sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* ids,
-                                     int n, double* y, double* y2, double* t_fine, double* t_coarse,
-                                     mlmc_sample_info* info, char* ws, cudaStream_t st_f,
-                                     cudaStream_t st_c) {
+mlmc_status mlmc::sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* seeds,
+                                    const uint64_t* ids, const double* stim, int n, double* y,
+                                    double* y2, double* t_fine, double* t_coarse,
+                                    mlmc_sample_info* info, char* ws, cudaStream_t st_f,
+                                    cudaStream_t st_c) {
   PairWs w = pair_ws(ctx, level, n);
   double* xi = (double*)(ws + w.xi);
   double* Zf = (double*)(ws + w.Zf);
   double* tf = t_fine ? t_fine : (double*)(ws + w.tf);
   mlmc_sample_info* inf = info ? info : (mlmc_sample_info*)(ws + w.info);
-  CK(ctx, launch_xi(seed, level, ids, n, ctx->M, xi, st_f));
+  CK(ctx, launch_xi(seed, seeds, level, ids, n, ctx->M, xi, st_f));
   ctx->launches += 1;
   mlmc_status r;
   if ((r = mlmc_kl_field(ctx, level, xi, n, Zf, st_f)) != MLMC_OK) return r;
@@ -439,10 +521,12 @@ static mlmc_status sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, co
     tc = t_coarse ? t_coarse : (double*)(ws + w.tc);
     if ((r = mlmc_kl_field(ctx, level - 1, xi, n, Zc, st_f)) != MLMC_OK) return r;
     if ((r = order_after(ctx, st_f, st_c)) != MLMC_OK) return r;
-    if ((r = solve_into(ctx, level - 1, Zc, n, tc, nullptr, inf + n, ws + w.solve_c, st_c)) != MLMC_OK)
+    if ((r = solve_into(ctx, level - 1, Zc, n, tc, nullptr, inf + n, ws + w.solve_c, st_c, stim)) !=
+        MLMC_OK)
       return r;
   }
-  if ((r = solve_into(ctx, level, Zf, n, tf, nullptr, inf, ws + w.solve_f, st_f)) != MLMC_OK) return r;
+  if ((r = solve_into(ctx, level, Zf, n, tf, nullptr, inf, ws + w.solve_f, st_f, stim)) != MLMC_OK)
+    return r;
   if (level > 0 && (r = order_after(ctx, st_c, st_f)) != MLMC_OK) return r;
   CK(ctx, launch_pair_diff(ctx->lv[0], ctx->lv[level], level > 0 ? &ctx->lv[level - 1] : nullptr, tf,
                            tc, n, y, y2, st_f));
@@ -461,8 +545,8 @@ extern "C" mlmc_status mlmc_sample_level(mlmc_ctx* ctx, int level, uint64_t seed
   if (!check_ws(ctx, ws, ws_bytes, pair_ws(ctx, level, n).total)) return MLMC_ERR_WORKSPACE;
   if (n == 0) return MLMC_OK;
   ctx->sync_used = 0;
-  return sample_level_into(ctx, level, seed, ids, n, y, y2, t_fine, t_coarse, info, (char*)ws,
-                           (cudaStream_t)stream, ctx->aux_pub);
+  return sample_level_into(ctx, level, seed, nullptr, ids, nullptr, n, y, y2, t_fine, t_coarse, info,
+                           (char*)ws, (cudaStream_t)stream, ctx->aux_pub);
 }
 
 extern "C" mlmc_status mlmc_reset(mlmc_ctx* ctx, void* stream) {
@@ -488,10 +572,9 @@ extern "C" mlmc_status mlmc_accumulate(mlmc_ctx* ctx, int level, const double* y
   return MLMC_OK;
 }
 
-extern "C" mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean_l,
-                                     double* var_l, double* V_l, int64_t* N_l, double* rmse,
-                                     void* stream) {
-  if (!ctx) return MLMC_ERR_ARG;
+mlmc_status mlmc::estimate_impl(mlmc_ctx* ctx, double* mean, double* var, double* mean_l,
+                                double* var_l, double* V_l, int64_t* N_l, double* rmse,
+                                double* bias, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   int L = ctx->cfg.n_levels;
   int64_t n0 = ctx->lv[0].nodes;
@@ -512,8 +595,16 @@ extern "C" mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, d
   const double* Vp = p + 2 * n0 + 2 * (int64_t)L * n0;
   if (V_l) memcpy(V_l, Vp, sizeof(double) * L);
   if (N_l) memcpy(N_l, Nh.data(), sizeof(int64_t) * L);
+  if (bias) *bias = Vp[L];
   if (rmse) *rmse = Vp[L + 1];
   return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean_l,
+                                     double* var_l, double* V_l, int64_t* N_l, double* rmse,
+                                     void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  return estimate_impl(ctx, mean, var, mean_l, var_l, V_l, N_l, rmse, nullptr, stream);
 }
 
 // --------------------------------------------------------------- whole run
@@ -541,56 +632,56 @@ extern "C" mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, const int64
   return MLMC_OK;
 }
 
-extern "C" mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed, int batch,
-                                void* ws, size_t ws_bytes, double* mean, double* var, double* V_l,
-                                double* C_l, double* rmse, double* stats, void* stream) {
-  if (!ctx) return MLMC_ERR_ARG;
-  if (!N_l || batch < 1 || batch > 65535) return fail(ctx, MLMC_ERR_ARG, "mlmc_run: bad arguments");
-  int L = ctx->cfg.n_levels;
-  for (int l = 0; l < L; ++l)
-    if (N_l[l] < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_run: negative sample count");
-  if (!check_ws(ctx, ws, ws_bytes, run_ws(ctx, N_l, batch))) return MLMC_ERR_WORKSPACE;
-  cudaStream_t st = (cudaStream_t)stream;
-  mlmc_status r = mlmc_reset(ctx, stream);
-  if (r != MLMC_OK) return r;
+// Runs count[l] level-l pairs with sample ids first[l] .. first[l]+count[l]-1
+// for every level, accumulating into the context's running estimates (no
+// reset).  Every level runs on its own pair of context streams, concurrently
+// with the others; within a level the fine and coarse solves of a batch run
+// concurrently.  Ordered after the work already on st; st waits for it all.
+// lvl_ms (host [levels] or NULL) receives each level's summed solve-kernel
+// time in ms (the solves of its pairs, fine and coarse).
+static mlmc_status run_levels(mlmc_ctx* ctx, const int64_t* first_id, const int64_t* count,
+                              uint64_t seed, int batch, char* ws, cudaStream_t st, double* lvl_ms) {
+  const int L = ctx->cfg.n_levels;
+  mlmc_status r;
+  const size_t ev0 = ctx->ev_used;
   ctx->prof = true;
-  ctx->ev_used = 0;
-  ctx->sync_used = 0;
-  ctx->launches = 0;
   struct ProfOff { mlmc_ctx* c; ~ProfOff() { c->prof = false; } } prof_off{ctx};
-  cudaEvent_t ev[2 * MLMC_MAX_LEVELS];
-  for (int l = 0; l < 2 * L; ++l) CK(ctx, cudaEventCreate(&ev[l]));
-  struct EvFree { cudaEvent_t* e; int n; ~EvFree() { for (int i = 0; i < n; ++i) cudaEventDestroy(e[i]); } }
-      ev_free{ev, 2 * L};
-  // every level runs on its own pair of streams, concurrently with the others
-  char* p = (char*)ws;
+  char* p = ws;
   for (int l = 0; l < L; ++l) {
     cudaStream_t sf = ctx->lvl_stream[2 * l], sc = ctx->lvl_stream[2 * l + 1];
-    const int nbl = level_batch(N_l[l], batch);
+    const int nbl = level_batch(count[l], batch);
     char* q = p;
     uint64_t* ids = (uint64_t*)q; q += align256((size_t)nbl * 8);
     double* y = (double*)q; q += align256((size_t)nbl * ctx->lv[0].nodes * 8);
     double* y2 = (double*)q; q += align256((size_t)nbl * ctx->lv[0].nodes * 8);
     p += level_run_ws(ctx, l, nbl);
+    if (count[l] == 0) continue;
     if ((r = order_after(ctx, st, sf)) != MLMC_OK) return r;
-    CK(ctx, cudaEventRecord(ev[2 * l], sf));
-    for (int64_t first = 0; first < N_l[l]; first += nbl) {
-      int nb = (int)((N_l[l] - first) < nbl ? (N_l[l] - first) : nbl);
-      CK(ctx, launch_iota((uint64_t)first, nb, ids, sf));
+    ctx->prof_level = l;
+    for (int64_t done = 0; done < count[l]; done += nbl) {
+      int nb = (int)((count[l] - done) < nbl ? (count[l] - done) : nbl);
+      CK(ctx, launch_iota((uint64_t)(first_id[l] + done), nb, ids, sf));
       ctx->launches += 1;
-      if ((r = sample_level_into(ctx, l, seed, ids, nb, y, y2, nullptr, nullptr, nullptr, q, sf, sc)) != MLMC_OK)
+      if ((r = sample_level_into(ctx, l, seed, nullptr, ids, nullptr, nb, y, y2, nullptr, nullptr, nullptr,
+                                 q, sf, sc)) != MLMC_OK)
         return r;
       if ((r = mlmc_accumulate(ctx, l, y, y2, nb, sf)) != MLMC_OK) return r;
     }
-    CK(ctx, cudaEventRecord(ev[2 * l + 1], sf));
     if ((r = order_after(ctx, sf, st)) != MLMC_OK) return r;
   }
-  if ((r = mlmc_estimate(ctx, mean, var, nullptr, nullptr, V_l, nullptr, rmse, stream)) != MLMC_OK) return r;
-  for (int l = 0; l < L; ++l) {
-    float ms = 0.f;
-    CK(ctx, cudaEventElapsedTime(&ms, ev[2 * l], ev[2 * l + 1]));
-    if (C_l) C_l[l] = N_l[l] > 0 ? ms * 1e-3 / (double)N_l[l] : 0.0;
+  if (lvl_ms) {
+    CK(ctx, cudaStreamSynchronize(st));
+    for (int l = 0; l < L; ++l) lvl_ms[l] = 0.0;
+    for (size_t i = ev0; i + 1 < ctx->ev_used; i += 2) {
+      float ms = 0.f;
+      CK(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+      lvl_ms[ctx->ev_level[i / 2]] += ms;
+    }
   }
+  return MLMC_OK;
+}
+
+static mlmc_status fill_stats(mlmc_ctx* ctx, double* stats) {
   unsigned long long cnt[N_COUNTERS];
   CK(ctx, cudaMemcpy(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
   if (stats) {
@@ -612,8 +703,188 @@ extern "C" mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed
   }
   if (cnt[0]) {
     char b[96];
-    snprintf(b, sizeof b, "mlmc_run: %llu sample solves did not converge", cnt[0]);
+    snprintf(b, sizeof b, "%llu sample solves did not converge", cnt[0]);
     return fail(ctx, MLMC_ERR_NOT_CONVERGED, b);
+  }
+  return MLMC_OK;
+}
+
+static mlmc_status run_begin(mlmc_ctx* ctx, void* stream) {
+  mlmc_status r = mlmc_reset(ctx, stream);
+  if (r != MLMC_OK) return r;
+  ctx->ev_used = 0;
+  ctx->ev_level.clear();
+  ctx->sync_used = 0;
+  ctx->launches = 0;
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed, int batch,
+                                void* ws, size_t ws_bytes, double* mean, double* var, double* V_l,
+                                double* C_l, double* rmse, double* stats, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (!N_l || batch < 1 || batch > 65535) return fail(ctx, MLMC_ERR_ARG, "mlmc_run: bad arguments");
+  const int L = ctx->cfg.n_levels;
+  for (int l = 0; l < L; ++l)
+    if (N_l[l] < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_run: negative sample count");
+  if (!check_ws(ctx, ws, ws_bytes, run_ws(ctx, N_l, batch))) return MLMC_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  mlmc_status r;
+  if ((r = run_begin(ctx, stream)) != MLMC_OK) return r;
+  int64_t first[MLMC_MAX_LEVELS] = {};
+  double lvl_ms[MLMC_MAX_LEVELS];
+  if ((r = run_levels(ctx, first, N_l, seed, batch, (char*)ws, st, lvl_ms)) != MLMC_OK) return r;
+  if ((r = mlmc_estimate(ctx, mean, var, nullptr, nullptr, V_l, nullptr, rmse, stream)) != MLMC_OK) return r;
+  for (int l = 0; l < L; ++l)
+    if (C_l) C_l[l] = N_l[l] > 0 ? lvl_ms[l] * 1e-3 / (double)N_l[l] : 0.0;
+  return fill_stats(ctx, stats);
+}
+
+extern "C" mlmc_status mlmc_run_more(mlmc_ctx* ctx, const int64_t* first_id, const int64_t* count,
+                                     uint64_t seed, int batch, void* ws, size_t ws_bytes,
+                                     double* solve_seconds, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (!first_id || !count || batch < 1 || batch > 65535)
+    return fail(ctx, MLMC_ERR_ARG, "mlmc_run_more: bad arguments");
+  const int L = ctx->cfg.n_levels;
+  for (int l = 0; l < L; ++l)
+    if (count[l] < 0 || first_id[l] < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_run_more: negative id or count");
+  if (!check_ws(ctx, ws, ws_bytes, run_ws(ctx, count, batch))) return MLMC_ERR_WORKSPACE;
+  ctx->ev_used = 0;
+  ctx->ev_level.clear();
+  ctx->sync_used = 0;
+  double lvl_ms[MLMC_MAX_LEVELS];
+  mlmc_status r = run_levels(ctx, first_id, count, seed, batch, (char*)ws, (cudaStream_t)stream, lvl_ms);
+  if (r != MLMC_OK) return r;
+  if (solve_seconds)
+    for (int l = 0; l < L; ++l) solve_seconds[l] = lvl_ms[l] * 1e-3;
+  return fill_stats(ctx, nullptr);
+}
+
+extern "C" mlmc_status mlmc_run_to_rmse(mlmc_ctx* ctx, double eps, const int64_t* N_pilot,
+                                        int max_rounds, int64_t max_per_level, uint64_t seed,
+                                        int batch, void* ws, size_t ws_bytes, int64_t* N_l,
+                                        double* mean, double* var, double* V_l, double* C_l,
+                                        double* rmse, double* bias, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  const int L = ctx->cfg.n_levels;
+  if (!(eps > 0.0) || !N_pilot || !N_l || max_rounds < 0 || max_per_level < 1 || batch < 1 ||
+      batch > 65535)
+    return fail(ctx, MLMC_ERR_ARG, "mlmc_run_to_rmse: bad arguments");
+  int64_t cap[MLMC_MAX_LEVELS];
+  for (int l = 0; l < L; ++l) {
+    if (N_pilot[l] < 1) return fail(ctx, MLMC_ERR_ARG, "mlmc_run_to_rmse: every level needs a pilot sample");
+    cap[l] = batch;
+  }
+  if (!check_ws(ctx, ws, ws_bytes, run_ws(ctx, cap, batch))) return MLMC_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  mlmc_status r;
+  if ((r = run_begin(ctx, stream)) != MLMC_OK) return r;
+  int64_t first[MLMC_MAX_LEVELS] = {}, cnt[MLMC_MAX_LEVELS];
+  double lvl_ms[MLMC_MAX_LEVELS], ms_total[MLMC_MAX_LEVELS] = {}, V[MLMC_MAX_LEVELS], Cl[MLMC_MAX_LEVELS];
+  for (int l = 0; l < L; ++l) { cnt[l] = N_pilot[l] < max_per_level ? N_pilot[l] : max_per_level; N_l[l] = 0; }
+  // Giles' allocation (Operations Research 56, 2008): with variance V_l and
+  // cost C_l per pair, N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k))
+  // makes sum_l V_l / N_l <= eps^2 / 2 at least total cost.
+  for (int round = 0;; ++round) {
+    ctx->ev_used = 0;
+    ctx->ev_level.clear();
+    ctx->sync_used = 0;
+    if ((r = run_levels(ctx, first, cnt, seed, batch, (char*)ws, st, lvl_ms)) != MLMC_OK) return r;
+    for (int l = 0; l < L; ++l) {
+      N_l[l] += cnt[l];
+      first[l] += cnt[l];
+      ms_total[l] += lvl_ms[l];
+    }
+    if ((r = fill_stats(ctx, nullptr)) != MLMC_OK) return r;
+    if ((r = mlmc_estimate(ctx, nullptr, nullptr, nullptr, nullptr, V, nullptr, nullptr, stream)) != MLMC_OK)
+      return r;
+    double S = 0.0;
+    for (int l = 0; l < L; ++l) {
+      Cl[l] = ms_total[l] * 1e-3 / (double)N_l[l];
+      S += sqrt(V[l] * Cl[l]);
+    }
+    if (round >= max_rounds) break;
+    int64_t more = 0;
+    for (int l = 0; l < L; ++l) {
+      double want = Cl[l] > 0.0 ? ceil(2.0 / (eps * eps) * sqrt(V[l] / Cl[l]) * S) : (double)N_l[l];
+      int64_t target = want > (double)max_per_level ? max_per_level : (int64_t)want;
+      cnt[l] = target > N_l[l] ? target - N_l[l] : 0;
+      more += cnt[l];
+    }
+    if (more == 0) break;
+  }
+  if ((r = estimate_impl(ctx, mean, var, nullptr, nullptr, V_l, nullptr, rmse, bias, stream)) != MLMC_OK)
+    return r;
+  if (C_l)
+    for (int l = 0; l < L; ++l) C_l[l] = Cl[l];
+  return MLMC_OK;
+}
+
+// ----------------------------------------------------------------- state
+extern "C" mlmc_status mlmc_get_state(mlmc_ctx* ctx, int64_t* N_l, double* mean_l, double* m2_l,
+                                      double* mean2_l, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  const int L = ctx->cfg.n_levels;
+  const int64_t n0 = ctx->lv[0].nodes;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* out[3] = {mean_l, m2_l, mean2_l};
+  for (int q = 0; q < 3; ++q)
+    if (out[q])
+      CK(ctx, cudaMemcpyAsync(out[q], ctx->d_acc + (int64_t)q * L * n0, sizeof(double) * L * n0,
+                              cudaMemcpyDeviceToHost, st));
+  CK(ctx, cudaStreamSynchronize(st));
+  if (N_l)
+    for (int l = 0; l < L; ++l) N_l[l] = ctx->N_acc[l];
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_set_state(mlmc_ctx* ctx, const int64_t* N_l, const double* mean_l,
+                                      const double* m2_l, const double* mean2_l, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (!N_l || !mean_l || !m2_l || !mean2_l) return fail(ctx, MLMC_ERR_ARG, "mlmc_set_state: NULL input");
+  const int L = ctx->cfg.n_levels;
+  const int64_t n0 = ctx->lv[0].nodes;
+  for (int l = 0; l < L; ++l)
+    if (N_l[l] < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_set_state: negative count");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* in[3] = {mean_l, m2_l, mean2_l};
+  for (int q = 0; q < 3; ++q)
+    CK(ctx, cudaMemcpyAsync(ctx->d_acc + (int64_t)q * L * n0, in[q], sizeof(double) * L * n0,
+                            cudaMemcpyHostToDevice, st));
+  CK(ctx, cudaStreamSynchronize(st));
+  for (int l = 0; l < L; ++l) ctx->N_acc[l] = N_l[l];
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_merge_states(int levels, int64_t nodes0, int64_t* N_a, double* mean_a,
+                                         double* m2_a, double* mean2_a, const int64_t* N_b,
+                                         const double* mean_b, const double* m2_b,
+                                         const double* mean2_b) {
+  if (levels < 1 || levels > MLMC_MAX_LEVELS || nodes0 < 1 || !N_a || !mean_a || !m2_a || !mean2_a ||
+      !N_b || !mean_b || !m2_b || !mean2_b)
+    return MLMC_ERR_ARG;
+  for (int l = 0; l < levels; ++l) {
+    const int64_t na = N_a[l], nb = N_b[l];
+    if (na < 0 || nb < 0) return MLMC_ERR_ARG;
+    if (nb == 0) continue;
+    const int64_t off = (int64_t)l * nodes0;
+    if (na == 0) {
+      for (int64_t i = 0; i < nodes0; ++i) {
+        mean_a[off + i] = mean_b[off + i];
+        m2_a[off + i] = m2_b[off + i];
+        mean2_a[off + i] = mean2_b[off + i];
+      }
+    } else {
+      const double dna = (double)na, dnb = (double)nb, nt = dna + dnb;
+      for (int64_t i = 0; i < nodes0; ++i) {
+        const double delta = mean_b[off + i] - mean_a[off + i];
+        mean_a[off + i] += delta * dnb / nt;
+        m2_a[off + i] += m2_b[off + i] + delta * delta * dna * dnb / nt;
+        mean2_a[off + i] += (mean2_b[off + i] - mean2_a[off + i]) * dnb / nt;
+      }
+    }
+    N_a[l] = na + nb;
   }
   return MLMC_OK;
 }

@@ -32,6 +32,7 @@ struct Physics {
   double Lz;
   double stim_r2;        // squared stimulus radius
   double stim_c[3];
+  const double* stim_ps; // per-sample stimulus centres, device [n][3], or NULL
 };
 
 struct SolverParams {
@@ -79,8 +80,8 @@ __device__ inline double rxn_d(const Physics& p, double u) {
 }
 
 // Kernels and launchers (defined in the .cu files).
-cudaError_t launch_xi(uint64_t seed, int level, const uint64_t* ids, int n, int M, double* xi,
-                      cudaStream_t st);
+cudaError_t launch_xi(uint64_t seed, const uint64_t* seeds, int level, const uint64_t* ids, int n,
+                      int M, double* xi, cudaStream_t st);
 cudaError_t launch_kl_field(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
                             const double* phi_x, const double* phi_y, const double* phi_z,
                             int n1d, const double* xi, int n, double* Z, cudaStream_t st);
@@ -96,15 +97,31 @@ cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverPar
 struct ClusterPlan {
   int C, H, nt;
   bool coef_smem;
+  bool gm;        // vectors in global memory (H = nodes per CTA), else shared (H = rows per CTA)
   size_t smem;
 };
-bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan);
+// Global-memory vectors of the gm layout, per sample: u [2N], F [N] (FP64),
+// r z p q d diag diag^-1 [7N] in the CG's precision, node codes [N].
+struct ClusterGlobal {
+  double* u = nullptr;
+  double* F = nullptr;
+  void* kr = nullptr;
+  unsigned* code = nullptr;
+};
+bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm = false);
 size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt);
+// Loads the kernel instance a plan launches and sets its attributes, so that
+// a timed launch does not include module loading.
+cudaError_t preload_solve_cluster(const LevelDesc& lv, bool mixed, const ClusterPlan& pl);
+cudaError_t preload_solve(const LevelDesc& lv, bool mixed);
+// How many clusters of a plan can be resident at once on this device (0: the
+// plan cannot launch here).
+cudaError_t cluster_max_active(const LevelDesc& lv, bool mixed, const ClusterPlan& pl, int* count);
 cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                                  bool mixed, const ClusterPlan& pl, int n, const double* coef64,
                                  const float* coef32, double* slab, double* t_act,
                                  mlmc_sample_info* info, unsigned long long* counters,
-                                 cudaStream_t st);
+                                 const ClusterGlobal& g, cudaStream_t st);
 // counters (device, may be NULL): [0] non-converged solves, [1] CG iterations x
 // nodes, [2] Newton iterations x nodes, [3] CG truncations, [4] halvings,
 // [5] CG iterations x nodes run in FP64 (the others run in FP32).

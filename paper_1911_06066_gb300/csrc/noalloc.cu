@@ -106,6 +106,7 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int level, con
   ph.Lz = c.dim == 3 ? c.L[2] : 1.0;
   ph.stim_r2 = c.stim_r * c.stim_r;
   for (int d = 0; d < 3; ++d) ph.stim_c[d] = c.stim_c[d];
+  ph.stim_ps = nullptr;
   // FP32 inner solves only where c dt max r' <= mixed_cdr_max, as in mlmc_solve
   const double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
   const double cdr_lim = c.mixed_cdr_max > 0.0 ? c.mixed_cdr_max : 2.0;

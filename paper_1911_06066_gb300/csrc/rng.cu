@@ -87,13 +87,14 @@ __device__ void sincos_2pi_series(double u, double* s_out, double* c_out) {
 }
 
 // One thread per (sample, mode pair).
-__global__ void xi_kernel(uint64_t seed, int level, const uint64_t* __restrict__ ids, int n, int M,
-                          double* __restrict__ xi) {
+__global__ void xi_kernel(uint64_t seed0, const uint64_t* __restrict__ seeds, int level,
+                          const uint64_t* __restrict__ ids, int n, int M, double* __restrict__ xi) {
   int pairs = (M + 1) / 2;
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)n * pairs) return;
   int s = (int)(g / pairs), j = (int)(g % pairs);
   uint64_t id = ids[s];
+  const uint64_t seed = seeds ? seeds[s] : seed0;
   uint32_t w[4];
   philox4x32_10((uint32_t)j, (uint32_t)id, (uint32_t)(id >> 32), (uint32_t)level, (uint32_t)seed,
                 (uint32_t)(seed >> 32), w);
@@ -109,12 +110,12 @@ __global__ void xi_kernel(uint64_t seed, int level, const uint64_t* __restrict__
   if (2 * j + 1 < M) xi[(int64_t)s * M + 2 * j + 1] = __dmul_rn(r, sn);
 }
 
-cudaError_t launch_xi(uint64_t seed, int level, const uint64_t* ids, int n, int M, double* xi,
-                      cudaStream_t st) {
+cudaError_t launch_xi(uint64_t seed, const uint64_t* seeds, int level, const uint64_t* ids, int n,
+                      int M, double* xi, cudaStream_t st) {
   int64_t total = (int64_t)n * ((M + 1) / 2);
   if (total == 0) return cudaSuccess;
   int bs = 128;
-  xi_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(seed, level, ids, n, M, xi);
+  xi_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(seed, seeds, level, ids, n, M, xi);
   return cudaGetLastError();
 }
 

@@ -125,12 +125,14 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
 
   // initial state: the stimulus ball; activation 0 where already >= 1/2
   double* u0 = sl ? sl : ub;
+  double sc[3];
+  for (int dd = 0; dd < 3; ++dd) sc[dd] = ph.stim_ps ? ph.stim_ps[3 * s + dd] : ph.stim_c[dd];
   for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {
     int i, j, k;
     node_ijk(lv, A, i, j, k);
     double x[3] = {i * lv.h[0], j * lv.h[1], k * lv.h[2]};
     double r2 = 0.0;
-    for (int dd = 0; dd < DIM; ++dd) r2 += (x[dd] - ph.stim_c[dd]) * (x[dd] - ph.stim_c[dd]);
+    for (int dd = 0; dd < DIM; ++dd) r2 += (x[dd] - sc[dd]) * (x[dd] - sc[dd]);
     double v = r2 < ph.stim_r2 ? 1.0 : 0.0;
     u0[A] = v;
     ta[A] = v >= 0.5 ? 0.0 : -1.0;
@@ -297,6 +299,15 @@ cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverPar
                                                            Ku, Kd, (double*)kr, t_act, info, counters);
   }
   return cudaGetLastError();
+}
+
+cudaError_t preload_solve(const LevelDesc& lv, bool mixed) {
+  cudaFuncAttributes a;
+  if (mixed)
+    return lv.dim == 3 ? cudaFuncGetAttributes(&a, solve_kernel<float, 3>)
+                       : cudaFuncGetAttributes(&a, solve_kernel<float, 2>);
+  return lv.dim == 3 ? cudaFuncGetAttributes(&a, solve_kernel<double, 3>)
+                     : cudaFuncGetAttributes(&a, solve_kernel<double, 2>);
 }
 
 }  // namespace mlmc

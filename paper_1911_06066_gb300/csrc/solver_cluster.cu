@@ -19,6 +19,14 @@
 //
 // Only the per-sample couplings (read once per Newton step by the residual)
 // and the outputs stay in global memory.
+//
+// Large grids (the 3D levels) do not fit a cluster's shared memory.  For them
+// the same kernel runs with its vectors in global memory (GM = true): each
+// sample's vectors are contiguous, CTA r of the cluster owns the contiguous
+// node range [rH, min((r+1)H, N)) (H nodes, not whole rows), a stencil reads
+// its neighbours at constant offsets from the node, and the cluster barriers
+// (release / acquire at cluster scope) publish each vector to the other CTAs.
+// The reductions stay in shared memory and DSMEM.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -45,6 +53,7 @@ __device__ __forceinline__ double wmax(double v) {
 struct Band {
   int C, rank, H, row0, row1, rowlen, nrows, nb, nmax;
   int N0, N1, N2;
+  int base;   // first node of this CTA
 };
 
 // A per-node shared-memory vector and the same vector of the two neighbour
@@ -56,18 +65,19 @@ struct View {
   const T* next;
 };
 
-template <typename T>
+template <bool GM, typename T>
 __device__ __forceinline__ View<T> make_view(cg::cluster_group& cl, const Band& b, T* p) {
   View<T> v;
   v.loc = p;
-  v.prev = b.rank > 0 ? cl.map_shared_rank(p, b.rank - 1) : nullptr;
-  v.next = b.rank < b.C - 1 ? cl.map_shared_rank(p, b.rank + 1) : nullptr;
+  v.prev = !GM && b.rank > 0 ? cl.map_shared_rank(p, b.rank - 1) : nullptr;
+  v.next = !GM && b.rank < b.C - 1 ? cl.map_shared_rank(p, b.rank + 1) : nullptr;
   return v;
 }
 
 // sum_o c[o] v[neighbour o] for the node (i, j, k); out-of-domain neighbours
-// have zero couplings and are skipped.  c(o) returns the coupling.
-template <int DIM, typename TA, typename TV, typename CF>
+// have zero couplings and are skipped.  c(o) returns the coupling.  With GM
+// the vector is contiguous over the sample and v.loc points at node b.base.
+template <int DIM, bool GM, typename TA, typename TV, typename CF>
 __device__ __forceinline__ TA stencil_band(const Band& b, const View<TV>& v, int i, int j, int k,
                                            CF c) {
   TA y = 0;
@@ -79,7 +89,8 @@ __device__ __forceinline__ TA stencil_band(const Band& b, const View<TV>& v, int
     const int row = DIM == 3 ? kk : jj;
     const int inrow = DIM == 3 ? jj * b.N0 + ii : ii;
     TV val;
-    if (row >= b.row0 && row < b.row1) val = v.loc[(row - b.row0) * b.rowlen + inrow];
+    if (GM) val = v.loc[row * b.rowlen + inrow - b.base];
+    else if (row >= b.row0 && row < b.row1) val = v.loc[(row - b.row0) * b.rowlen + inrow];
     else if (row < b.row0) val = v.prev[(b.H - 1) * b.rowlen + inrow];
     else val = v.next[inrow];
     y += (TA)c(o) * (TA)val;
@@ -207,11 +218,12 @@ size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt)
   return smem_layout(dim, nmax, mixed ? 4 : 8, coef_smem, nt).total;
 }
 
-template <typename KR, int DIM, int NT, int NPT>
+template <typename KR, int DIM, int NT, int NPT, bool GM>
 __global__ void __launch_bounds__(NT, 1)
 solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict__ coef64,
                      const KR* __restrict__ coefK, int H, int coef_smem, double* slab,
-                     double* t_act, mlmc_sample_info* info, unsigned long long* counters) {
+                     double* t_act, mlmc_sample_info* info, unsigned long long* counters,
+                     double* g_u, double* g_F, KR* g_kr, unsigned* g_code) {
   constexpr int NO = DIM == 3 ? 27 : 9;
   constexpr int CTR = DIM == 3 ? 13 : 4;
   cg::cluster_group cl = cg::this_cluster();
@@ -222,29 +234,39 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   b.rowlen = DIM == 3 ? b.N0 * b.N1 : b.N0;
   b.nrows = DIM == 3 ? b.N2 : b.N1;
   b.H = H;
-  b.row0 = min(b.rank * H, b.nrows);
-  b.row1 = min(b.row0 + H, b.nrows);
-  b.nb = (b.row1 - b.row0) * b.rowlen;
-  b.nmax = H * b.rowlen;
   const int s = blockIdx.x / b.C;
   const int N = (int)lv.nodes;
-  const int base = b.row0 * b.rowlen;
+  if (GM) {
+    // H nodes per CTA, contiguous
+    b.base = min(b.rank * H, N);
+    b.nb = min(H, N - b.base);
+    b.row0 = b.row1 = 0;
+    b.nmax = H;
+  } else {
+    b.row0 = min(b.rank * H, b.nrows);
+    b.row1 = min(b.row0 + H, b.nrows);
+    b.nb = (b.row1 - b.row0) * b.rowlen;
+    b.nmax = H * b.rowlen;
+    b.base = b.row0 * b.rowlen;
+  }
+  const int base = b.base;
   const int nmax = b.nmax;
   const int N01 = b.N0 * b.N1;
   const int tid = threadIdx.x;
 
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(DIM, nmax, (int)sizeof(KR), coef_smem != 0, NT);
-  double* ubuf0 = (double*)(smem + L.u0);
-  double* ubuf1 = (double*)(smem + L.u1);
-  double* F = (double*)(smem + L.F);
-  KR* r = (KR*)(smem + L.r);
-  KR* z = (KR*)(smem + L.z);
-  KR* p = (KR*)(smem + L.p);
-  KR* q = (KR*)(smem + L.q);
-  KR* d = (KR*)(smem + L.d);
-  KR* hm = (KR*)(smem + L.hm);
-  KR* pinv = (KR*)(smem + L.pinv);
+  const SmemLayout L = smem_layout(DIM, GM ? 0 : nmax, (int)sizeof(KR), !GM && coef_smem != 0, NT);
+  double* ubuf0 = GM ? g_u + (int64_t)s * 2 * N + base : (double*)(smem + L.u0);
+  double* ubuf1 = GM ? g_u + (int64_t)s * 2 * N + N + base : (double*)(smem + L.u1);
+  double* F = GM ? g_F + (int64_t)s * N + base : (double*)(smem + L.F);
+  KR* const kr0 = GM ? g_kr + (int64_t)s * 7 * N + base : nullptr;
+  KR* r = GM ? kr0 : (KR*)(smem + L.r);
+  KR* z = GM ? kr0 + N : (KR*)(smem + L.z);
+  KR* p = GM ? kr0 + 2 * N : (KR*)(smem + L.p);
+  KR* q = GM ? kr0 + 3 * N : (KR*)(smem + L.q);
+  KR* d = GM ? kr0 + 4 * N : (KR*)(smem + L.d);
+  KR* hm = GM ? kr0 + 5 * N : (KR*)(smem + L.hm);
+  KR* pinv = GM ? kr0 + 6 * N : (KR*)(smem + L.pinv);
   KR* cs = (KR*)(smem + L.cs);                             // couplings [NO][nmax] if coef_smem
   double* red = (double*)(smem + L.red);
   double* slot = (double*)(smem + L.slot);
@@ -260,15 +282,23 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   // Per node: packed coordinates i | j << 11 | k << 22 and, in bit 31, whether
   // every neighbour lies inside the domain and inside this band (then the
   // stencil uses constant local offsets).
-  unsigned* code = (unsigned*)(smem + L.code);
+  unsigned* code = GM ? g_code + (int64_t)s * N + base : (unsigned*)(smem + L.code);
   for (int a = tid; a < b.nb; a += NT) {
-    const int lr = a / b.rowlen, inrow = a - lr * b.rowlen;
-    const int row = b.row0 + lr;
-    int i, j, k;
-    if (DIM == 3) { k = row; j = inrow / b.N0; i = inrow - j * b.N0; }
-    else { k = 0; j = row; i = inrow; }
+    int i, j, k, row;
+    if (GM) {
+      const int A = base + a;
+      i = A % b.N0;
+      j = (A / b.N0) % b.N1;
+      k = A / N01;
+      row = DIM == 3 ? k : j;
+    } else {
+      const int lr = a / b.rowlen, inrow = a - lr * b.rowlen;
+      row = b.row0 + lr;
+      if (DIM == 3) { k = row; j = inrow / b.N0; i = inrow - j * b.N0; }
+      else { k = 0; j = row; i = inrow; }
+    }
     bool in = i > 0 && i < b.N0 - 1 && j > 0 && j < b.N1 - 1 && (DIM == 2 || (k > 0 && k < b.N2 - 1));
-    bool fast = in && row > b.row0 && row < b.row1 - 1;
+    bool fast = in && (GM || (row > b.row0 && row < b.row1 - 1));
     code[a] = (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22) | (fast ? 0x80000000u : 0u);
   }
 #define CI(c) ((int)((c) & 2047u))
@@ -278,24 +308,26 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
 
   cl.sync();   // every CTA of the cluster is resident before any DSMEM access
 
-  if (coef_smem)
+  if (!GM && coef_smem)
     for (int o = 0; o < NO; ++o)
       for (int a = tid; a < b.nb; a += NT) cs[o * nmax + a] = cKg[(int64_t)o * N + base + a];
+  double sc[3];
+  for (int dd = 0; dd < 3; ++dd) sc[dd] = ph.stim_ps ? ph.stim_ps[3 * s + dd] : ph.stim_c[dd];
   for (int a = tid; a < b.nb; a += NT) {
     const unsigned c = code[a];
     const int A = base + a;
     double x[3] = {CI(c) * lv.h[0], CJ(c) * lv.h[1], CK_(c) * lv.h[2]};
     double r2 = 0.0;
-    for (int dd = 0; dd < DIM; ++dd) r2 += (x[dd] - ph.stim_c[dd]) * (x[dd] - ph.stim_c[dd]);
+    for (int dd = 0; dd < DIM; ++dd) r2 += (x[dd] - sc[dd]) * (x[dd] - sc[dd]);
     double v = r2 < ph.stim_r2 ? 1.0 : 0.0;
     ubuf0[a] = v;
     ta[A] = v >= 0.5 ? 0.0 : -1.0;
     if (sl) sl[A] = v;
   }
-  const View<KR> pv = make_view(cl, b, p);
-  const View<KR> dv = make_view(cl, b, d);
-  const View<double> uv0 = make_view(cl, b, ubuf0);
-  const View<double> uv1 = make_view(cl, b, ubuf1);
+  const View<KR> pv = make_view<GM>(cl, b, p);
+  const View<KR> dv = make_view<GM>(cl, b, d);
+  const View<double> uv0 = make_view<GM>(cl, b, ubuf0);
+  const View<double> uv1 = make_view<GM>(cl, b, ubuf1);
   const double rtol2 = sp.lin_rtol * sp.lin_rtol;
 
   int status = MLMC_OK, failed_step = 0;
@@ -316,7 +348,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         const int A = base + a;
         auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
         const double ku = CFAST(c) ? stencil_fast<DIM, double>(u, a, b.N0, N01, c64A)
-                                   : stencil_band<DIM, double>(b, uv, CI(c), CJ(c), CK_(c), c64A);
+                                   : stencil_band<DIM, GM, double>(b, uv, CI(c), CJ(c), CK_(c), c64A);
         const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c)), uA = u[a];
         const double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
         F[a] = f;
@@ -349,14 +381,14 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
             const unsigned c = code[a];
             const int A = base + a;
             KR hp;
-            if (coef_smem) {
+            if (!GM && coef_smem) {
               auto cf = [=](int o) { return cs[o * nmax + a]; };
               hp = CFAST(c) ? stencil_fast<DIM, KR>(p, a, b.N0, N01, cf)
-                            : stencil_band<DIM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
+                            : stencil_band<DIM, GM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
             } else {
               auto cf = [=](int o) { return cKg[(int64_t)o * N + A]; };
               hp = CFAST(c) ? stencil_fast<DIM, KR>(p, a, b.N0, N01, cf)
-                            : stencil_band<DIM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
+                            : stencil_band<DIM, GM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
             }
             const KR pa = p[a];
             const KR qv = hp + hm[a] * pa;
@@ -429,7 +461,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           const int A = base + a;
           auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
           const double kd = CFAST(c) ? stencil_fast<DIM, double>(d, a, b.N0, N01, c64A)
-                                     : stencil_band<DIM, double>(b, dv, CI(c), CJ(c), CK_(c), c64A);
+                                     : stencil_band<DIM, GM, double>(b, dv, CI(c), CJ(c), CK_(c), c64A);
           const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c));
           const double uA = u[a], da = (double)d[a], d2 = da * da;
           const double r1 = ph.c * (-3.0 * uA * uA + 2.0 * (1.0 + ph.a) * uA - ph.a);
@@ -502,11 +534,27 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
 }
 
 // Launch plan: the smallest cluster whose bands fit the shared memory (or the
-// requested size want_C), and the block size.  Returns false when it does not fit.
-bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan) {
+// requested size want_C), and the block size.  Returns false when it does not
+// fit.  With gm the vectors live in global memory: any C works, and C = 0
+// picks clusters of 16 CTAs, or fewer for grids of at most 8192 nodes.
+bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm) {
   const int rowlen = lv.dim == 3 ? lv.N[0] * lv.N[1] : lv.N[0];
   const int nrows = lv.dim == 3 ? lv.N[2] : lv.N[1];
   const size_t limit = 224 * 1024;
+  if (gm) {
+    int C = want_C;
+    if (!C) {
+      C = 16;
+      while (C > 1 && (int64_t)C * 512 > lv.nodes) C /= 2;
+    }
+    plan->C = C;
+    plan->H = (int)((lv.nodes + C - 1) / C);
+    plan->nt = 512;
+    plan->coef_smem = false;
+    plan->gm = true;
+    plan->smem = smem_layout(lv.dim, 0, mixed ? 4 : 8, false, 512).total;
+    return true;
+  }
   for (int C = 1; C <= 16; C *= 2) {
     if (want_C && C != want_C) continue;
     int H = (nrows + C - 1) / C;
@@ -517,61 +565,102 @@ bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan
     size_t bytes = cluster_smem_bytes(lv.dim, nmax, mixed, coef, nt);
     if (bytes > limit) continue;
     plan->C = C; plan->H = H; plan->nt = nt; plan->coef_smem = coef; plan->smem = bytes;
+    plan->gm = false;
     return true;
   }
   return false;
 }
 
-template <typename KR, int DIM, int NT, int NPT>
-static cudaError_t launch_one(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
-                              const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
-                              double* slab, double* t_act, mlmc_sample_info* info,
-                              unsigned long long* counters, cudaStream_t st) {
-  auto kern = solve_cluster_kernel<KR, DIM, NT, NPT>;
+template <typename KR, int DIM, bool GM>
+static cudaError_t set_attrs(const ClusterPlan& pl) {
+  auto kern = solve_cluster_kernel<KR, DIM, 512, 5, GM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-  if (e != cudaSuccess) return e;
-  if (pl.C > 8) {
+  if (e == cudaSuccess && pl.C > 8)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
+  return e;
+}
+
+static cudaLaunchConfig_t launch_cfg(const ClusterPlan& pl, int n, cudaStream_t st,
+                                     cudaLaunchAttribute* at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n * pl.C));
-  cfg.blockDim = dim3(NT);
+  cfg.blockDim = dim3(512);
   cfg.dynamicSmemBytes = pl.smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = pl.C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, lv, ph, sp, coef64, coefK, pl.H, pl.coef_smem ? 1 : 0, slab,
-                            t_act, info, counters);
+  return cfg;
+}
+
+template <typename KR, int DIM, bool GM>
+static cudaError_t launch_one(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
+                              const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
+                              double* slab, double* t_act, mlmc_sample_info* info,
+                              unsigned long long* counters, const ClusterGlobal& g,
+                              cudaStream_t st) {
+  cudaError_t e = set_attrs<KR, DIM, GM>(pl);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = launch_cfg(pl, n, st, at);
+  return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<KR, DIM, 512, 5, GM>, lv, ph, sp, coef64, coefK,
+                            pl.H, pl.coef_smem ? 1 : 0, slab, t_act, info, counters, g.u, g.F,
+                            (KR*)g.kr, g.code);
 }
 
 template <typename KR, int DIM>
 static cudaError_t launch_nt(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                              const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
                              double* slab, double* t_act, mlmc_sample_info* info,
-                             unsigned long long* counters, cudaStream_t st) {
-  return launch_one<KR, DIM, 512, 5>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info, counters, st);
+                             unsigned long long* counters, const ClusterGlobal& g, cudaStream_t st) {
+  if (pl.gm)
+    return launch_one<KR, DIM, true>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info, counters, g, st);
+  return launch_one<KR, DIM, false>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info, counters, g, st);
+}
+
+template <typename KR, int DIM>
+static cudaError_t preload_one(const ClusterPlan& pl) {
+  return pl.gm ? set_attrs<KR, DIM, true>(pl) : set_attrs<KR, DIM, false>(pl);
+}
+
+template <typename KR, int DIM>
+static cudaError_t max_clusters_one(const ClusterPlan& pl, int* count) {
+  cudaError_t e = preload_one<KR, DIM>(pl);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = launch_cfg(pl, 1, nullptr, at);
+  return pl.gm ? cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, true>, &cfg)
+               : cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, false>, &cfg);
+}
+
+cudaError_t preload_solve_cluster(const LevelDesc& lv, bool mixed, const ClusterPlan& pl) {
+  if (mixed) return lv.dim == 3 ? preload_one<float, 3>(pl) : preload_one<float, 2>(pl);
+  return lv.dim == 3 ? preload_one<double, 3>(pl) : preload_one<double, 2>(pl);
+}
+
+cudaError_t cluster_max_active(const LevelDesc& lv, bool mixed, const ClusterPlan& pl, int* count) {
+  if (mixed) return lv.dim == 3 ? max_clusters_one<float, 3>(pl, count) : max_clusters_one<float, 2>(pl, count);
+  return lv.dim == 3 ? max_clusters_one<double, 3>(pl, count) : max_clusters_one<double, 2>(pl, count);
 }
 
 cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                                  bool mixed, const ClusterPlan& pl, int n, const double* coef64,
                                  const float* coef32, double* slab, double* t_act,
                                  mlmc_sample_info* info, unsigned long long* counters,
-                                 cudaStream_t st) {
+                                 const ClusterGlobal& g, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  if (pl.gm && (!g.u || !g.F || !g.kr || !g.code)) return cudaErrorInvalidValue;
   if (mixed) {
     if (lv.dim == 3)
-      return launch_nt<float, 3>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, st);
-    return launch_nt<float, 2>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, st);
+      return launch_nt<float, 3>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, st);
+    return launch_nt<float, 2>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, st);
   }
   if (lv.dim == 3)
-    return launch_nt<double, 3>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, st);
-  return launch_nt<double, 2>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, st);
+    return launch_nt<double, 3>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, st);
+  return launch_nt<double, 2>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, st);
 }
 
 }  // namespace mlmc

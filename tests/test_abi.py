@@ -60,3 +60,51 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         B.lib()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C sizes and field
+    offsets (compiled with the host C compiler from include/mlmc.h)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no host C compiler")
+    structs = [("mlmc_config", B.mlmc_config), ("mlmc_sample_info", B.mlmc_sample_info),
+               ("mlmc_server_config", B.mlmc_server_config), ("mlmc_request", B.mlmc_request),
+               ("mlmc_result", B.mlmc_result)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mlmc.h"', "int main(void) {"]
+    for name, cls in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs:
+        assert int(got[name]) == C.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(got[name + "." + f[0]]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_server_rejects_bad_arguments_without_device_work(lib):
+    assert lib.mlmc_server_create(None, None, None) == -1
+    assert lib.mlmc_server_submit(None, None, 0) == -1
+    cnt = C.c_int()
+    assert lib.mlmc_server_poll(None, None, 0, C.byref(cnt), None, None, 0, 0.0) == -1
+    assert lib.mlmc_server_drain(None, 1.0) == -1
+    lib.mlmc_server_destroy(None)
+
+
+def test_merge_is_host_only(lib):
+    # runs with no device present: the cross-device merge needs none
+    import numpy as np
+    Na, Nb = np.array([2], np.int64), np.array([2], np.int64)
+    ma, mb = np.array([1.0, 3.0]), np.array([3.0, 5.0])
+    za, zb = np.zeros(2), np.zeros(2)
+    qa, qb = np.ones(2), np.full(2, 3.0)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    assert lib.mlmc_merge_states(1, 2, p(Na), p(ma), p(za), p(qa), p(Nb), p(mb), p(zb), p(qb)) == 0
+    assert Na[0] == 4 and list(ma) == [2.0, 4.0] and list(za) == [4.0, 4.0] and list(qa) == [2.0, 2.0]

@@ -1,0 +1,206 @@
+"""Incremental runs, accumulator state (checkpoint / resume, the cross-device
+merge emulated with several contexts on one device) and the adaptive sample
+allocation, through the C ABI, against a single fixed-count run and the CPU
+oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import oracle_levels, small_workload
+from paper_1911_06066_gb300 import binding as B
+from paper_1911_06066_gb300 import distributed as D
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1911_06066_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def workload():
+    return small_workload(n0=(4, 4), m0=16, levels=2, M=8, stim_r=0.3, s_l0=0.02, s_t=0.005,
+                          sigma2=0.25, T=1.5)
+
+
+def ctx_for(w, precision=B.MLMC_PREC_FP64):
+    return B.Context(B.make_config(w, precision))
+
+
+def assert_same_estimate(a, b, rtol=1e-12):
+    np.testing.assert_array_equal(a["N_l"], b["N_l"])
+    np.testing.assert_allclose(a["mean"], b["mean"], rtol=rtol, atol=1e-13)
+    np.testing.assert_allclose(a["var"], b["var"], rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(a["V_l"], b["V_l"], rtol=1e-10)
+    assert math.isclose(a["rmse"], b["rmse"], rel_tol=1e-10)
+
+
+def test_run_more_in_chunks_equals_one_run():
+    w = workload()
+    N = [24, 10]
+    ref_ctx = ctx_for(w)
+    ref_ctx.run(N, seed=3, batch=7)
+    ref = ref_ctx.estimate()
+    ctx = ctx_for(w)
+    ctx.reset()
+    secs = ctx.run_more([0, 0], [5, 10], seed=3, batch=3)
+    assert np.all(secs > 0)
+    ctx.run_more([5, 10], [19, 0], seed=3, batch=8)
+    assert_same_estimate(ctx.estimate(), ref)
+
+
+def test_state_round_trip():
+    w = workload()
+    ctx = ctx_for(w)
+    ctx.run([9, 4], seed=2, batch=4)
+    s = ctx.get_state()
+    assert list(s.N) == [9, 4]
+    e1 = ctx.estimate()
+    other = ctx_for(w)
+    other.set_state(s)
+    e2 = other.estimate()
+    for k in ("mean", "var", "V_l"):
+        np.testing.assert_array_equal(e1[k], e2[k])
+    ctx.reset()
+    assert list(ctx.get_state().N) == [0, 0]
+
+
+def test_sharded_contexts_merge_to_one_run():
+    """The multi-device schedule on one device: three contexts (ranks) run
+    disjoint id shards one after the other; their states, merged in rank
+    order on the host, give the estimate of one run over all ids."""
+    w = workload()
+    N = [23, 7]
+    ref_ctx = ctx_for(w)
+    ref_ctx.run(N, seed=5, batch=6)
+    ref = ref_ctx.estimate()
+    states = []
+    for r in range(3):
+        c = ctx_for(w)
+        c.reset()
+        f, n = D.shard(N, r, 3)
+        c.run_more(f, n, seed=5, batch=4)
+        states.append(c.get_state())
+    merged = D.merge_in_order(states)
+    out = ctx_for(w)
+    out.set_state(merged)
+    assert_same_estimate(out.estimate(), ref)
+
+
+def test_checkpoint_resume_equals_uninterrupted(tmp_path):
+    w = workload()
+    N = [16, 6]
+    ref_ctx = ctx_for(w)
+    ref_ctx.run(N, seed=9, batch=5)
+    ref = ref_ctx.estimate()
+    a = ctx_for(w)
+    a.reset()
+    a.run_more([0, 0], [7, 2], seed=9, batch=5)
+    p = str(tmp_path / "ck.npz")
+    D.save_checkpoint(p, a.get_state(), [7, 2], 9, meta={"workload": w["name"]})
+    del a
+    st, nxt, seed, meta = D.load_checkpoint(p)
+    b = ctx_for(w)
+    b.set_state(st)
+    b.run_more(nxt, np.array(N) - nxt, seed=seed, batch=5)
+    assert_same_estimate(b.estimate(), ref)
+
+
+@pytest.mark.parametrize("precision", [B.MLMC_PREC_FP64, B.MLMC_PREC_MIXED], ids=["fp64", "mixed"])
+def test_run_to_rmse_allocation_and_estimate(precision):
+    w = workload()
+    ctx = ctx_for(w, precision)
+    pilot = ctx.run([16, 8], seed=4, batch=8)
+    # a target that needs tens of samples per level
+    eps = math.sqrt(2.0 * (pilot["V_l"][0] / 60.0 + pilot["V_l"][1] / 20.0))
+    cap = 400
+    res = ctx.run_to_rmse(eps, [16, 8], max_rounds=6, max_per_level=cap, seed=4, batch=32)
+    N, V, Cl = res["N_l"], res["V_l"], res["C_l"]
+    assert np.all(N >= [16, 8]) and np.all(N <= cap)
+    assert np.all(Cl > 0) and np.all(V >= 0)
+    # the stopping rule: every level holds at least its optimal count for the
+    # final V_l, C_l (or the cap), hence sum V_l / N_l <= eps^2 / 2
+    S = float(np.sum(np.sqrt(V * Cl)))
+    for l in range(2):
+        want = math.ceil(2.0 / eps ** 2 * math.sqrt(V[l] / Cl[l]) * S)
+        assert N[l] >= min(want, cap) or N[l] == cap
+    if np.all(N < cap):
+        assert float(np.sum(V / N)) <= eps ** 2 / 2 * (1 + 1e-12)
+    # the estimate is the fixed-count estimator over ids 0..N_l-1
+    lvs = oracle_levels(w, newton_max=500)
+    est = O.mlmc_estimate(lvs, w["sigma2"], w["ell"], w["M"], 4, [int(n) for n in N], threads=8)
+    tol = 1e-6 if precision == B.MLMC_PREC_FP64 else 1e-4
+    np.testing.assert_allclose(res["mean"], est["mean"], atol=tol * w["T"])
+    np.testing.assert_allclose(V, est["V_l"], rtol=1e-4, atol=1e-8)
+    assert math.isclose(res["bias"], est["bias"], rel_tol=1e-4, abs_tol=1e-8)
+    assert math.isclose(res["rmse"], math.sqrt(float(np.sum(V / N)) + res["bias"] ** 2), rel_tol=1e-10)
+
+
+def test_run_to_rmse_pilot_only_and_errors():
+    w = workload()
+    ctx = ctx_for(w)
+    res = ctx.run_to_rmse(1.0, [6, 3], max_rounds=0, seed=1, batch=4)
+    assert list(res["N_l"]) == [6, 3]
+    ref = ctx_for(w)
+    ref.run([6, 3], seed=1, batch=4)
+    np.testing.assert_allclose(res["mean"], ref.estimate()["mean"], rtol=1e-12, atol=1e-13)
+    with pytest.raises(B.MLMCError, match="ERR_ARG"):
+        ctx.run_to_rmse(0.0, [6, 3])
+    with pytest.raises(B.MLMCError, match="ERR_ARG"):
+        ctx.run_to_rmse(1.0, [6, 0])
+    with pytest.raises(B.MLMCError, match="ERR_ARG"):
+        ctx.run_more([0, -1], [1, 1])
+
+
+@pytest.mark.parametrize("precision", [B.MLMC_PREC_FP64, B.MLMC_PREC_MIXED], ids=["fp64", "mixed"])
+def test_autotune_picks_a_timed_layout_and_keeps_results(precision):
+    w = workload()
+    ctx = ctx_for(w, precision)
+    assert ctx.layout(1) == 0
+    best, ms = ctx.autotune(1, 6, seed=2)
+    assert best in ms and -1 in ms and 1 in ms
+    assert all(v > 0 for v in ms.values())
+    assert ms[best] == min(ms.values())
+    assert ctx.layout(1) == best
+    # every layout solves the same discrete problem: the estimate agrees with
+    # an untuned context to rounding
+    res = ctx.run([8, 6], seed=3, batch=4)
+    ref = ctx_for(w, precision).run([8, 6], seed=3, batch=4)
+    tol = 1e-9 if precision == B.MLMC_PREC_FP64 else 1e-4
+    np.testing.assert_allclose(res["mean"], ref["mean"], atol=tol * w["T"])
+
+
+@pytest.mark.parametrize("layout", [-1, 1, 2, 4, 8, 16])
+def test_every_layout_matches_oracle(layout):
+    w = workload()
+    ctx = ctx_for(w)
+    ctx.set_layout(1, layout)
+    assert ctx.layout(1) == layout
+    lv = oracle_levels(w, newton_max=500)[1]
+    ids = torch.arange(0, 3, dtype=torch.int64)
+    xi = ctx.xi(7, 1, ids)
+    Z = ctx.kl_field(1, xi)
+    t, slab, info = ctx.solve(1, Z, slab=True)
+    torch.cuda.synchronize()
+    for r in range(3):
+        assert B.info_dicts(info)[r]["status"] == 0
+        Zo = O.kl_field(w["dim"], w["L"], list(lv.n)[:w["dim"]], w["sigma2"], w["ell"], w["M"],
+                        O.xi(7, 1, r, w["M"]))[0]
+        so, to, _ = O.solve_sample(lv, Zo)
+        assert np.abs(slab[r].cpu().numpy() - so).max() <= 1e-8
+        near = (np.abs(so - 0.5) < 1e-6).any(axis=0)
+        assert np.abs(t[r].cpu().numpy() - to)[~near].max() <= 1e-6 * w["T"]
+
+
+def test_set_layout_rejects_bad_values():
+    ctx = ctx_for(workload())
+    for bad in (3, 32, -2):
+        with pytest.raises(B.MLMCError, match="ERR_ARG"):
+            ctx.set_layout(0, bad)
+    with pytest.raises(B.MLMCError, match="ERR_ARG"):
+        ctx.set_layout(5, 1)

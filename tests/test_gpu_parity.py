@@ -35,7 +35,23 @@ def ctx_for(w, precision=B.MLMC_PREC_FP64, **kw):
     return B.Context(B.make_config(w, precision, **kw))
 
 
-LAYOUTS = [pytest.param(B.MLMC_SOLVER_BLOCK, id="block"), pytest.param(B.MLMC_SOLVER_CLUSTER, id="cluster")]
+# solve layouts: the block-per-sample kernel, the automatic cluster layout
+# (shared memory where a band fits), and global-memory clusters of 16 and 2 CTAs
+LAYOUTS = [pytest.param("block", id="block"), pytest.param("cluster", id="cluster"),
+           pytest.param("gm16", id="gm16"), pytest.param("gm2", id="gm2")]
+LAYOUT_CODE = {"gm16": 116, "gm2": 102}
+
+
+def layout_ctx(w, layout, precision=B.MLMC_PREC_FP64, **kw):
+    """A context whose every level uses the named layout."""
+    solver = {"block": B.MLMC_SOLVER_BLOCK}.get(layout, B.MLMC_SOLVER_CLUSTER)
+    if layout in (B.MLMC_SOLVER_AUTO, B.MLMC_SOLVER_BLOCK, B.MLMC_SOLVER_CLUSTER):
+        solver = layout
+    ctx = B.Context(B.make_config(w, precision, solver=solver, **kw))
+    if layout in LAYOUT_CODE:
+        for l in range(w["levels"]):
+            ctx.set_layout(l, LAYOUT_CODE[layout])
+    return ctx
 
 
 def ambiguous_nodes(slab, thr=0.5, eps=1e-6):
@@ -46,7 +62,7 @@ def ambiguous_nodes(slab, thr=0.5, eps=1e-6):
 
 def compare_solve(w, level, sample_ids, seed=0, precision=B.MLMC_PREC_FP64, u_tol=U_TOL,
                   t_tol=T_TOL, solver=B.MLMC_SOLVER_AUTO):
-    ctx = ctx_for(w, precision, solver=solver)
+    ctx = layout_ctx(w, solver, precision)
     ids = torch.tensor(sample_ids, dtype=torch.int64)
     xi = ctx.xi(seed, level, ids)
     Z = ctx.kl_field(level, xi)
@@ -228,7 +244,7 @@ def test_strongly_indefinite_steps_give_valid_roots(solver):
     satisfies its residual and is a local minimum of its step energy."""
     w = small_workload(n0=(6, 6), m0=8, levels=1, M=8, stim_r=0.3, s_l0=0.02, s_t=0.005,
                        sigma2=0.25, T=1.5)
-    ctx = ctx_for(w, solver=solver)
+    ctx = layout_ctx(w, solver)
     ids = [0, 1, 5]
     Z = ctx.kl_field(0, ctx.xi(9, 0, torch.tensor(ids)))
     t, slab, info = ctx.solve(0, Z, slab=True)
