@@ -149,7 +149,18 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
     double dmax = 0.0;
     for (int i = 0; i < n; ++i) if (fabs(d[i]) > dmax) dmax = fabs(d[i]);
     double alpha = 1.0;
-    if (dmax > step_max) alpha = step_max / dmax;
+    if (dmax > step_max) {
+      /* max-norm trust region: clip every component to [-step_max, step_max];
+         if the clipped direction is not a descent direction of E, scale the
+         whole direction to max |d| = step_max instead */
+      double gdc = 0.0;
+      for (int i = 0; i < n; ++i) gdc += F[i] * fmin(fmax(d[i], -step_max), step_max);
+      if (gdc < 0.0) {
+        for (int i = 0; i < n; ++i) d[i] = fmin(fmax(d[i], -step_max), step_max);
+      } else {
+        alpha = step_max / dmax;
+      }
+    }
     if (dmax > lv->newton_tol && dmax > 1e-6) {
       double gd = dot(n, F, d);
       or_stiff_apply(lv, Kst, u, Ku);

@@ -183,7 +183,7 @@ class State:
         return self
 
 
-def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=500, lin_rtol=1e-12,
+def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, lin_rtol=1e-12,
                 lin_max=5000, levels=None, solver=MLMC_SOLVER_AUTO, mixed_cdr_max=0.0,
                 cluster_size=0):
     """mlmc_config from a workload dictionary (see workloads.py)."""

@@ -216,7 +216,21 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
       for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) dmax_loc = fmax(dmax_loc, fabs((double)d[A]));
       const double dmax = block_max(dmax_loc, sh);
       double alpha = 1.0;
-      if (dmax > sp.step_max) alpha = sp.step_max / dmax;
+      if (dmax > sp.step_max) {
+        // max-norm trust region: clip every component, or scale the whole
+        // direction if the clipped one is not a descent direction
+        const KR lim = (KR)sp.step_max;
+        double gdc_loc = 0.0;
+        for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS)
+          gdc_loc += F[A] * (double)fmin(fmax(d[A], -lim), lim);
+        const double gdc = block_sum(gdc_loc, sh);
+        if (gdc < 0.0) {
+          for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) d[A] = fmin(fmax(d[A], -lim), lim);
+          __syncthreads();
+        } else {
+          alpha = sp.step_max / dmax;
+        }
+      }
       if (dmax > sp.newton_tol && dmax > sp.ls_full_step) {
         double gd_loc = 0.0;
         for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {

@@ -447,7 +447,20 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       }
       const double dmax = bc[0];
       double alpha = 1.0;
-      if (dmax > sp.step_max) alpha = sp.step_max / dmax;
+      if (dmax > sp.step_max) {
+        // max-norm trust region: clip every component, or scale the whole
+        // direction if the clipped one is not a descent direction
+        const KR lim = (KR)sp.step_max;
+        double g1[1] = {0.0};
+        for (int a = tid; a < b.nb; a += NT) g1[0] += F[a] * (double)fmin(fmax(d[a], -lim), lim);
+        cluster_reduce<NT, double, 1>(g1, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+        if (bc[0] < 0.0) {
+          for (int a = tid; a < b.nb; a += NT) d[a] = fmin(fmax(d[a], -lim), lim);
+          cluster_barrier(cl, b.C);
+        } else {
+          alpha = sp.step_max / dmax;
+        }
+      }
       if (dmax > sp.newton_tol && dmax > sp.ls_full_step) {
         // The step energy is a quartic polynomial in the step length (R is a
         // quartic), so for every trial length al
