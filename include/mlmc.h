@@ -82,7 +82,32 @@ typedef struct {
                             c dt max r' <= mixed_cdr_max (<= 0 selects the default 2) */
   int cluster_size;      /* cluster layout: CTAs per sample (1, 2, 4, 8 or 16); 0 picks
                             the smallest that fits shared memory                        */
+  int precond;           /* mlmc_precond: preconditioner of the CG inner solves          */
+  int mg_nu;             /* MLMC_PRECOND_GMG: smoothing sweeps before and after the coarse
+                            correction, 0..8 (0 selects the default 2)                   */
+  int mg_coarse_sweeps;  /* MLMC_PRECOND_GMG: smoothing sweeps on the coarsest grid, 0..64
+                            (0 selects the default 8)                                    */
 } mlmc_config;
+
+/* Row a7 -- preconditioner of the Newton steps' CG (the paper's Krylov solver
+ * is preconditioned by ILU / block Jacobi on CPUs, Sec. 3.5).
+ * MLMC_PRECOND_JACOBI: z = r / |H_ii|.
+ * MLMC_PRECOND_GMG: one symmetric geometric-multigrid V-cycle on
+ *   K + diag(|M (1/dt - r'(u))|) over vertex-nested coarsenings of the level's
+ *   grid (every even cell count halved while the grid has more than 512 nodes):
+ *   linear interpolation P, restriction P^T, Galerkin coarse stiffness P^T K P,
+ *   lumped coarse diagonal P^T d, l1-Jacobi smoothing (mg_nu sweeps before and
+ *   after, mg_coarse_sweeps on the coarsest grid), in the CG's precision (FP32
+ *   in MLMC_PREC_MIXED).  It is used on levels whose step Hessians are
+ *   positive definite for every state (c dt max r' < 1, max r' =
+ *   c((1+a)^2/3 - a)), where the Newton direction and so the selected root do
+ *   not depend on the preconditioner; other levels keep Jacobi.  It runs in
+ *   the global-memory cluster layout (layout codes 100 + C), which the
+ *   automatic layout choice then selects. */
+typedef enum {
+  MLMC_PRECOND_JACOBI = 0,
+  MLMC_PRECOND_GMG = 1
+} mlmc_precond;
 
 typedef enum {
   MLMC_SOLVER_AUTO = 0,    /* cluster layout where a sample fits, else block layout      */
@@ -136,6 +161,19 @@ mlmc_status mlmc_xi(mlmc_ctx* ctx, uint64_t seed, int level, const uint64_t* ids
  * xi: device [n][kl_modes]; Z: device [n][cells_l]. */
 mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
                           void* stream);
+
+/* Row a2, mixed precision -- the same field as mlmc_kl_field computed as one
+ * dense contraction (cells x modes) . (modes x samples) on the tensor cores
+ * (tcgen05 kind::tf32, accumulators in tensor memory) with the three-term
+ * split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi of FP32 operands into TF32
+ * parts: FP32 accuracy (|error| <~ 1e-6 max|Z|), FP64 output.  Arguments as
+ * for mlmc_kl_field (n <= 65535 * 256).  MLMC_PREC_MIXED pipelines use it on
+ * the levels whose inner solves run in FP32; the others use mlmc_kl_field.
+ * A tile whose bounded wait for the tensor cores runs out leaves its outputs
+ * unwritten and is reported by the next mlmc_run / mlmc_run_more as
+ * MLMC_ERR_TIMEOUT. */
+mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
+                             void* stream);
 
 /* Rows a3-a8 -- per-sample solve on grid level l: conductivity from Z, Q1
  * assembly, implicit Euler over all m_l steps with Newton (Sec. 3.3, 3.5),

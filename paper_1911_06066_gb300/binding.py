@@ -30,10 +30,12 @@ class mlmc_config(C.Structure):
                 ("kl_sigma2", C.c_double), ("kl_ell", C.c_double), ("kl_modes", C.c_int),
                 ("precision", C.c_int), ("newton_tol", C.c_double), ("newton_max", C.c_int),
                 ("lin_rtol", C.c_double), ("lin_max", C.c_int), ("solver", C.c_int),
-                ("mixed_cdr_max", C.c_double), ("cluster_size", C.c_int)]
+                ("mixed_cdr_max", C.c_double), ("cluster_size", C.c_int), ("precond", C.c_int),
+                ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int)]
 
 
 MLMC_SOLVER_AUTO, MLMC_SOLVER_BLOCK, MLMC_SOLVER_CLUSTER = 0, 1, 2
+MLMC_PRECOND_JACOBI, MLMC_PRECOND_GMG = 0, 1
 
 
 class mlmc_sample_info(C.Structure):
@@ -87,6 +89,7 @@ def lib():
             "mlmc_workspace_bytes": ([vp, ip, ip, C.POINTER(sz)], ip),
             "mlmc_xi": ([vp, u64, ip, vp, ip, vp, vp], ip),
             "mlmc_kl_field": ([vp, ip, vp, ip, vp, vp], ip),
+            "mlmc_kl_field_tc": ([vp, ip, vp, ip, vp, vp], ip),
             "mlmc_solve": ([vp, ip, vp, ip, vp, vp, vp, vp, sz, vp], ip),
             "mlmc_slab_residual": ([vp, ip, vp, vp, ip, vp, vp, vp], ip),
             "mlmc_activation": ([vp, ip, vp, ip, vp, vp], ip),
@@ -127,7 +130,8 @@ def lib():
 def exported_symbols():
     """Names of the C-ABI functions this binding declares."""
     return ["mlmc_create", "mlmc_destroy", "mlmc_last_error", "mlmc_level_info",
-            "mlmc_workspace_bytes", "mlmc_xi", "mlmc_kl_field", "mlmc_solve", "mlmc_slab_residual",
+            "mlmc_workspace_bytes", "mlmc_xi", "mlmc_kl_field", "mlmc_kl_field_tc", "mlmc_solve",
+            "mlmc_slab_residual",
             "mlmc_activation", "mlmc_sample_level", "mlmc_accumulate", "mlmc_reset",
             "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_run_more",
             "mlmc_run_to_rmse", "mlmc_get_state", "mlmc_set_state", "mlmc_merge_states",
@@ -185,7 +189,7 @@ class State:
 
 def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, lin_rtol=1e-12,
                 lin_max=5000, levels=None, solver=MLMC_SOLVER_AUTO, mixed_cdr_max=0.0,
-                cluster_size=0):
+                cluster_size=0, precond=MLMC_PRECOND_JACOBI, mg_nu=0, mg_coarse_sweeps=0):
     """mlmc_config from a workload dictionary (see workloads.py)."""
     c = mlmc_config()
     c.dim = w["dim"]
@@ -205,6 +209,7 @@ def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, 
     c.solver = solver
     c.mixed_cdr_max = mixed_cdr_max
     c.cluster_size = cluster_size
+    c.precond, c.mg_nu, c.mg_coarse_sweeps = precond, mg_nu, mg_coarse_sweeps
     return c
 
 
@@ -285,6 +290,16 @@ class Context:
         xi = xi.contiguous()
         out = torch.empty((xi.shape[0], cells), dtype=torch.float64, device="cuda")
         self._check(lib().mlmc_kl_field(self.h, level, _p(xi), xi.shape[0], _p(out), _stream(stream)))
+        return out
+
+    def kl_field_tc(self, level, xi, stream=None):
+        """The field of kl_field on the tensor cores (split TF32, FP32 accuracy)."""
+        import torch
+        _, cells, _ = self.level_info(level)
+        xi = xi.contiguous()
+        out = torch.empty((xi.shape[0], cells), dtype=torch.float64, device="cuda")
+        self._check(lib().mlmc_kl_field_tc(self.h, level, _p(xi), xi.shape[0], _p(out),
+                                           _stream(stream)))
         return out
 
     def solve(self, level, Z, slab=False, stream=None):

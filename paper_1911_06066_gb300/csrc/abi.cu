@@ -53,13 +53,30 @@ static bool level_mixed(const mlmc_config& c, const LevelDesc& lv) {
   return lv.dt * rmax <= lim;
 }
 
+// Geometric multigrid preconditioner of a level (row a7): requested by
+// cfg.precond and used only where every step Hessian is positive definite,
+// c dt max r' < 1, so that the Newton-CG directions -- and the selected root --
+// do not depend on the preconditioner beyond the CG tolerance.  mg->G = 0 when
+// the level keeps Jacobi.
+static bool level_gmg(const mlmc_config& c, const LevelDesc& lv, MGDesc* mg) {
+  mg->G = 0;
+  mg->per_sample = 0;
+  if (c.precond != MLMC_PRECOND_GMG) return false;
+  double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
+  if (lv.dt * rmax >= 1.0) return false;
+  mg_hierarchy(lv, c.mg_nu > 0 ? c.mg_nu : 2, c.mg_coarse_sweeps > 0 ? c.mg_coarse_sweeps : 8, mg);
+  return true;
+}
+
 struct SolveWs {
-  size_t coef64, coef32, ubuf, F, Ku, Kd, kr, total;
+  size_t coef64, coef32, ubuf, F, Ku, Kd, kr, mg, total;
 };
 
-static SolveWs solve_ws(const LevelDesc& lv, int n, bool mixed) {
+static SolveWs solve_ws(const mlmc_config& c, const LevelDesc& lv, int n, bool mixed) {
   SolveWs w;
   size_t N = (size_t)lv.nodes, NO = (size_t)n_offsets(lv.dim), kr = mixed ? 4 : 8;
+  MGDesc mg;
+  level_gmg(c, lv, &mg);
   size_t off = 0;
   w.coef64 = off; off += align256((size_t)n * NO * N * 8);
   w.coef32 = off; off += mixed ? align256((size_t)n * NO * N * 4) : 0;
@@ -68,6 +85,7 @@ static SolveWs solve_ws(const LevelDesc& lv, int n, bool mixed) {
   w.Ku = off; off += align256((size_t)n * N * 8);
   w.Kd = off; off += align256((size_t)n * N * 8);
   w.kr = off; off += align256((size_t)n * 7 * N * kr);
+  w.mg = off; off += align256((size_t)n * (size_t)mg.per_sample * kr);
   w.total = off;
   return w;
 }
@@ -82,9 +100,9 @@ PairWs mlmc::pair_ws(const mlmc_ctx* c, int level, int n) {
   w.tf = off; off += align256((size_t)n * lf.nodes * 8);
   w.tc = off; off += level > 0 ? align256((size_t)n * c->lv[level - 1].nodes * 8) : 0;
   w.info = off; off += align256((size_t)2 * n * sizeof(mlmc_sample_info));
-  w.solve_f = off; off += solve_ws(lf, n, level_mixed(c->cfg, lf)).total;
+  w.solve_f = off; off += solve_ws(c->cfg, lf, n, level_mixed(c->cfg, lf)).total;
   w.solve_c = off;
-  if (level > 0) off += solve_ws(c->lv[level - 1], n, level_mixed(c->cfg, c->lv[level - 1])).total;
+  if (level > 0) off += solve_ws(c->cfg, c->lv[level - 1], n, level_mixed(c->cfg, c->lv[level - 1])).total;
   w.total = off;
   return w;
 }
@@ -124,6 +142,10 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   if (c.cluster_size != 0 && c.cluster_size != 1 && c.cluster_size != 2 && c.cluster_size != 4 &&
       c.cluster_size != 8 && c.cluster_size != 16)
     return fail(nullptr, MLMC_ERR_ARG, "cluster_size must be 0, 1, 2, 4, 8 or 16");
+  if (c.precond != MLMC_PRECOND_JACOBI && c.precond != MLMC_PRECOND_GMG)
+    return fail(nullptr, MLMC_ERR_ARG, "unknown preconditioner");
+  if (c.mg_nu < 0 || c.mg_nu > 8 || c.mg_coarse_sweeps < 0 || c.mg_coarse_sweeps > 64)
+    return fail(nullptr, MLMC_ERR_ARG, "mg_nu must be 0..8 and mg_coarse_sweeps 0..64");
 
   mlmc_ctx* ctx = new mlmc_ctx();
   ctx->cfg = c;
@@ -296,6 +318,29 @@ extern "C" mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi,
   return MLMC_OK;
 }
 
+extern "C" mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* xi, int n,
+                                        double* Z, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (bad_level(ctx, level)) return MLMC_ERR_ARG;
+  if (n < 0 || n > 65535 * 256 || (n > 0 && (!xi || !Z)))
+    return fail(ctx, MLMC_ERR_ARG, "mlmc_kl_field_tc: bad arguments");
+  CK(ctx, launch_kl_field_tc(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_idx,
+                             ctx->d_phi[level][0], ctx->d_phi[level][1], ctx->d_phi[level][2], xi,
+                             n, Z, ctx->d_cnt + 6, (cudaStream_t)stream));
+  ctx->launches += 1;
+  return MLMC_OK;
+}
+
+// The KL field of the pipeline: on the tensor cores (split TF32) on levels
+// whose inner solves run in FP32 (MLMC_PREC_MIXED and c dt max r' <=
+// mixed_cdr_max), in FP64 elsewhere -- where the root selection is sensitive
+// to perturbations of the field, the field stays exact to FP64 rounding.
+static mlmc_status kl_into(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
+                           cudaStream_t st) {
+  if (level_mixed(ctx->cfg, ctx->lv[level])) return mlmc_kl_field_tc(ctx, level, xi, n, Z, st);
+  return mlmc_kl_field(ctx, level, xi, n, Z, st);
+}
+
 // Coefficients + sweep for n samples of one level inside an already checked
 // workspace region.
 // The solve layout of a level: false = the block-per-sample kernel, else a
@@ -310,6 +355,8 @@ static bool choose_plan(const mlmc_ctx* ctx, const LevelDesc& lv, bool mixed, in
   if (want < 0 && ctx->cfg.solver == MLMC_SOLVER_AUTO) return false;
   if (want > 100) return cluster_plan(lv, mixed, want - 100, plan, true);
   if (want > 0 && cluster_plan(lv, mixed, want, plan)) return true;
+  MGDesc mg;
+  if (want == 0 && level_gmg(ctx->cfg, lv, &mg)) return cluster_plan(lv, mixed, 0, plan, true);
   if (cluster_plan(lv, mixed, 0, plan)) return true;
   return cluster_plan(lv, mixed, 0, plan, true);
 }
@@ -328,7 +375,7 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
   ph.stim_ps = stim;
   const LevelDesc& lv = ctx->lv[level];
   bool mixed = level_mixed(ctx->cfg, lv);
-  SolveWs w = solve_ws(lv, n, mixed);
+  SolveWs w = solve_ws(ctx->cfg, lv, n, mixed);
   double* coef64 = (double*)(ws + w.coef64);
   float* coef32 = mixed ? (float*)(ws + w.coef32) : nullptr;
   CK(ctx, launch_assemble(lv, ph, Z, n, coef64, coef32, st));
@@ -357,8 +404,11 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     g.F = (double*)(ws + w.F);
     g.kr = (void*)(ws + w.kr);
     g.code = (unsigned*)(ws + w.Ku);
+    MGDesc mg;
+    level_gmg(ctx->cfg, lv, &mg);
+    g.mg = mg.G > 0 ? (void*)(ws + w.mg) : nullptr;
     CK(ctx, launch_solve_cluster(lv, ph, sp, mixed, plan, n, coef64, coef32, slab, t_act, info,
-                                 ctx->d_cnt, g, st));
+                                 ctx->d_cnt, g, mg, st));
   }
   else
     CK(ctx, launch_solve(lv, ph, sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
@@ -376,7 +426,7 @@ extern "C" mlmc_status mlmc_solve(mlmc_ctx* ctx, int level, const double* Z, int
   if (bad_level(ctx, level)) return MLMC_ERR_ARG;
   if (n < 0 || n > 65535 || (n > 0 && (!Z || !t_act)))
     return fail(ctx, MLMC_ERR_ARG, "mlmc_solve: bad arguments");
-  size_t need = solve_ws(ctx->lv[level], n, level_mixed(ctx->cfg, ctx->lv[level])).total;
+  size_t need = solve_ws(ctx->cfg, ctx->lv[level], n, level_mixed(ctx->cfg, ctx->lv[level])).total;
   if (!check_ws(ctx, ws, ws_bytes, need)) return MLMC_ERR_WORKSPACE;
   if (n == 0) return MLMC_OK;
   return solve_into(ctx, level, Z, n, t_act, slab, info, (char*)ws, (cudaStream_t)stream);
@@ -514,12 +564,12 @@ mlmc_status mlmc::sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, con
   CK(ctx, launch_xi(seed, seeds, level, ids, n, ctx->M, xi, st_f));
   ctx->launches += 1;
   mlmc_status r;
-  if ((r = mlmc_kl_field(ctx, level, xi, n, Zf, st_f)) != MLMC_OK) return r;
+  if ((r = kl_into(ctx, level, xi, n, Zf, st_f)) != MLMC_OK) return r;
   double* tc = nullptr;
   if (level > 0) {
     double* Zc = (double*)(ws + w.Zc);
     tc = t_coarse ? t_coarse : (double*)(ws + w.tc);
-    if ((r = mlmc_kl_field(ctx, level - 1, xi, n, Zc, st_f)) != MLMC_OK) return r;
+    if ((r = kl_into(ctx, level - 1, xi, n, Zc, st_f)) != MLMC_OK) return r;
     if ((r = order_after(ctx, st_f, st_c)) != MLMC_OK) return r;
     if ((r = solve_into(ctx, level - 1, Zc, n, tc, nullptr, inf + n, ws + w.solve_c, st_c, stim)) !=
         MLMC_OK)
@@ -700,6 +750,11 @@ static mlmc_status fill_stats(mlmc_ctx* ctx, double* stats) {
     stats[6] = (double)cnt[0];
     stats[7] = (double)ctx->launches;
     stats[8] = (double)cnt[5];
+  }
+  if (cnt[6]) {
+    char b[96];
+    snprintf(b, sizeof b, "%llu KL tensor-core tiles timed out waiting for their MMAs", cnt[6]);
+    return fail(ctx, MLMC_ERR_TIMEOUT, b);
   }
   if (cnt[0]) {
     char b[96];

@@ -44,6 +44,33 @@ struct SolverParams {
   double step_max;       // largest nodal move per Newton iteration (inf: none)
 };
 
+// Geometric multigrid hierarchy of one grid level (the CG preconditioner of
+// the global-memory cluster layout).  Level 0 is the level's own grid; level
+// g+1 halves every axis of level g whose cell count is even (vertex-nested, so
+// coarse node I sits on fine node 2I).  Per sample the workspace holds, in the
+// CG's precision, at element offsets relative to the sample's block:
+//   level 0: ks (row sums of |K|), xa, xb (smoother ping-pong), t (residual);
+//   level g >= 1: K [3^dim][nodes] (Galerkin couplings), ks, d (lumped
+//   diagonal term), inv (l1-Jacobi inverse), xa, xb, b (right-hand side), t.
+constexpr int MG_MAX_LEVELS = 10;
+struct MGLevel {
+  int n[3];           // cells per axis
+  int N[3];           // nodes per axis
+  int nodes;
+  int cz[3];          // 1: axis halved from this level to the next
+  int64_t K, ks, d, inv, xa, xb, b, t;   // element offsets (K, d, inv, b unused on level 0)
+};
+struct MGDesc {
+  int G;              // levels (G = 0: no multigrid)
+  int nu;             // pre- and post-smoothing sweeps
+  int coarse_sweeps;  // l1-Jacobi sweeps on the coarsest level
+  int64_t per_sample; // elements per sample
+  MGLevel l[MG_MAX_LEVELS];
+};
+// Builds the hierarchy of grid lv: coarsen while some axis has an even cell
+// count and the grid has more than 512 nodes.
+void mg_hierarchy(const LevelDesc& lv, int nu, int coarse_sweeps, MGDesc* mg);
+
 // Root-selection step limit: on strongly indefinite steps (c dt max r' > 2,
 // max r' = c((1+a)^2/3 - a)) no node moves by more than 0.1 per Newton
 // iteration; elsewhere steps are not limited.
@@ -85,6 +112,13 @@ cudaError_t launch_xi(uint64_t seed, const uint64_t* seeds, int level, const uin
 cudaError_t launch_kl_field(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
                             const double* phi_x, const double* phi_y, const double* phi_z,
                             int n1d, const double* xi, int n, double* Z, cudaStream_t st);
+// Mixed-precision KL synthesis on the tensor cores (kl_tc.cu): three-term
+// split-TF32 products, FP32 accumulation in tensor memory, FP64 output.  err
+// (device) counts CTAs whose bounded wait for the tensor cores ran out.
+cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
+                               const double* phi_x, const double* phi_y, const double* phi_z,
+                               const double* xi, int n, double* Z, unsigned long long* err,
+                               cudaStream_t st);
 cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,
                             double* coef64, float* coef32, cudaStream_t st);
 cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
@@ -107,6 +141,7 @@ struct ClusterGlobal {
   double* F = nullptr;
   void* kr = nullptr;
   unsigned* code = nullptr;
+  void* mg = nullptr;     // multigrid workspace (MGDesc::per_sample elements per sample), or NULL
 };
 bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm = false);
 size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt);
@@ -117,15 +152,18 @@ cudaError_t preload_solve(const LevelDesc& lv, bool mixed);
 // How many clusters of a plan can be resident at once on this device (0: the
 // plan cannot launch here).
 cudaError_t cluster_max_active(const LevelDesc& lv, bool mixed, const ClusterPlan& pl, int* count);
+// mg: the multigrid hierarchy of lv (G > 0 and a gm plan: GMG-preconditioned
+// CG; otherwise Jacobi).
 cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                                  bool mixed, const ClusterPlan& pl, int n, const double* coef64,
                                  const float* coef32, double* slab, double* t_act,
                                  mlmc_sample_info* info, unsigned long long* counters,
-                                 const ClusterGlobal& g, cudaStream_t st);
+                                 const ClusterGlobal& g, const MGDesc& mg, cudaStream_t st);
 // counters (device, may be NULL): [0] non-converged solves, [1] CG iterations x
 // nodes, [2] Newton iterations x nodes, [3] CG truncations, [4] halvings,
-// [5] CG iterations x nodes run in FP64 (the others run in FP32).
-constexpr int N_COUNTERS = 6;
+// [5] CG iterations x nodes run in FP64 (the others run in FP32), [6] tensor-
+// core KL tiles whose bounded wait ran out.
+constexpr int N_COUNTERS = 7;
 cudaError_t launch_slab_residual(const LevelDesc& lv, const Physics& ph, const double* coef64,
                                  const double* slab, int n, double* F, double* res_max,
                                  cudaStream_t st);

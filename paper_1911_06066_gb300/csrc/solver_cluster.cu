@@ -1,550 +1,21 @@
-// Rows a4-a8 on thread-block clusters: the same per-sample Newton-CG sweep as
-// solver.cu (Sec. 3.3, Eq. mono_disc; Sec. 3.5 -- the algorithm, its root
-// selection rule and its stopping tests are documented there), laid out for
-// GB300's distributed shared memory.
-//
-// Mapping.  One cluster of C CTAs owns one sample.  The node grid is cut into
-// C bands of H whole rows (2D: rows of constant y; 3D: planes of constant z);
-// CTA r owns rows [rH, min((r+1)H, rows)).  Every per-node vector of the sweep
-// -- the FP64 state u (two slices) and residual F, the CG vectors r, z, p, q,
-// d, diag, diag^-1 (FP64, or FP32 in the mixed path), and, when they fit, the
-// couplings used by the CG in the CG's precision -- lives in the owning CTA's shared memory for
-// the whole time sweep.  A stencil touching the row above or below the band
-// reads the neighbour CTA's shared memory directly (DSMEM), so there is no
-// halo copy; the barrier that publishes a vector is the one the algorithm
-// needs anyway.  Dot products are reduced per warp, per CTA (fixed order),
-// then across the cluster by reading every CTA's partial in rank order, so the
-// result is identical on all CTAs and deterministic.  Per CG iteration the
-// cluster synchronises three times (p^T H p, r^T z, and the new p).
-//
-// Only the per-sample couplings (read once per Newton step by the residual)
-// and the outputs stay in global memory.
-//
-// Large grids (the 3D levels) do not fit a cluster's shared memory.  For them
-// the same kernel runs with its vectors in global memory (GM = true): each
-// sample's vectors are contiguous, CTA r of the cluster owns the contiguous
-// node range [rH, min((r+1)H, N)) (H nodes, not whole rows), a stencil reads
-// its neighbours at constant offsets from the node, and the cluster barriers
-// (release / acquire at cluster scope) publish each vector to the other CTAs.
-// The reductions stay in shared memory and DSMEM.
-#include <cooperative_groups.h>
-#include <math.h>
-
-#include "internal.cuh"
-
-namespace cg = cooperative_groups;
+// Host side of the cluster solver (solver_cluster.cuh): launch plans, kernel
+// attributes and the launches of the Jacobi-preconditioned instances; the
+// multigrid-preconditioned instances are compiled in solver_cluster_mg.cu.
+#include "solver_cluster.cuh"
 
 namespace mlmc {
 
-namespace {
-
-__device__ __forceinline__ double wsum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double wmax(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Band geometry of this CTA.
-struct Band {
-  int C, rank, H, row0, row1, rowlen, nrows, nb, nmax;
-  int N0, N1, N2;
-  int base;   // first node of this CTA
-};
-
-// A per-node shared-memory vector and the same vector of the two neighbour
-// CTAs (nullptr at the ends of the cluster).
-template <typename T>
-struct View {
-  T* loc;
-  const T* prev;
-  const T* next;
-};
-
-template <bool GM, typename T>
-__device__ __forceinline__ View<T> make_view(cg::cluster_group& cl, const Band& b, T* p) {
-  View<T> v;
-  v.loc = p;
-  v.prev = !GM && b.rank > 0 ? cl.map_shared_rank(p, b.rank - 1) : nullptr;
-  v.next = !GM && b.rank < b.C - 1 ? cl.map_shared_rank(p, b.rank + 1) : nullptr;
-  return v;
-}
-
-// sum_o c[o] v[neighbour o] for the node (i, j, k); out-of-domain neighbours
-// have zero couplings and are skipped.  c(o) returns the coupling.  With GM
-// the vector is contiguous over the sample and v.loc points at node b.base.
-template <int DIM, bool GM, typename TA, typename TV, typename CF>
-__device__ __forceinline__ TA stencil_band(const Band& b, const View<TV>& v, int i, int j, int k,
-                                           CF c) {
-  TA y = 0;
-#pragma unroll
-  for (int o = 0; o < (DIM == 3 ? 27 : 9); ++o) {
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
-    const int ii = i + dx, jj = j + dy, kk = k + dz;
-    if (ii < 0 || ii >= b.N0 || jj < 0 || jj >= b.N1 || kk < 0 || kk >= b.N2) continue;
-    const int row = DIM == 3 ? kk : jj;
-    const int inrow = DIM == 3 ? jj * b.N0 + ii : ii;
-    TV val;
-    if (GM) val = v.loc[row * b.rowlen + inrow - b.base];
-    else if (row >= b.row0 && row < b.row1) val = v.loc[(row - b.row0) * b.rowlen + inrow];
-    else if (row < b.row0) val = v.prev[(b.H - 1) * b.rowlen + inrow];
-    else val = v.next[inrow];
-    y += (TA)c(o) * (TA)val;
-  }
-  return y;
-}
-
-// Neighbour sum for a node whose 3^dim neighbours all lie inside the domain
-// and inside this CTA's band: constant local offsets.
-template <int DIM, typename TA, typename TV, typename CF>
-__device__ __forceinline__ TA stencil_fast(const TV* v, int a, int N0, int N01, CF c) {
-  TA y = 0;
-#pragma unroll
-  for (int o = 0; o < (DIM == 3 ? 27 : 9); ++o) {
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
-    y += (TA)c(o) * (TA)v[a + dx + dy * N0 + dz * N01];
-  }
-  return y;
-}
-
-// Deterministic cluster-wide sums (op 0) or maxima (op 1, of non-negative
-// values) of K values per thread.  Warps reduce by butterfly shuffles in TP
-// (float in the mixed CG, double otherwise); warp 0 combines the CTA's warps
-// by a fixed shuffle tree; lane q then stores the CTA's K partials into
-// CTA q's slot[par][k][rank] (remote stores in parallel), one cluster barrier
-// publishes them, and warp 0 of every CTA combines the C partials by the same
-// fixed tree -- so every CTA obtains identical totals.  Lane 0 writes the
-// totals to bc[0..K) and calls post(bc) to derive further scalars in bc[K..8).
-// Every thread reads bc[] after the call returns.
-template <typename TP>
-__device__ __forceinline__ TP combine(TP x, TP y, int op) { return op ? (x > y ? x : y) : x + y; }
-
-template <int NT, typename TP, int K, typename POST>
-__device__ __forceinline__ void cluster_reduce(TP (&v)[K], int op, double* red, double* slot,
-                                               double* bc, int& par, cg::cluster_group& cl, int C,
-                                               int rank, POST post) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] = combine(v[k], __shfl_xor_sync(0xffffffffu, v[k], o), op);
-    if (lane == 0) red[k * 32 + warp] = (double)v[k];
-  }
-  __syncthreads();
-  if (warp == 0) {
-    TP t[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      t[k] = lane < NT / 32 ? (TP)red[k * 32 + lane] : (TP)0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t[k] = combine(t[k], __shfl_xor_sync(0xffffffffu, t[k], o), op);
-    }
-    if (C == 1) {
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) bc[k] = (double)t[k];
-        post(bc);
-      }
-    } else if (lane < C) {
-      double* dst = cl.map_shared_rank(slot + par * 64 + rank, lane);
-#pragma unroll
-      for (int k = 0; k < K; ++k) dst[k * 16] = (double)t[k];
-    }
-  }
-  if (C > 1) {
-    cl.sync();
-    if (warp == 0) {
-      TP t[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        t[k] = lane < C ? (TP)slot[par * 64 + k * 16 + lane] : (TP)0;
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) t[k] = combine(t[k], __shfl_xor_sync(0xffffffffu, t[k], o), op);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) bc[k] = (double)t[k];
-        post(bc);
-      }
-    }
-  }
-  __syncthreads();
-  par ^= 1;
-}
-
-struct NoPost {
-  __device__ void operator()(double*) const {}
-};
-
-__device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl, int C) {
-  if (C == 1) __syncthreads(); else cl.sync();
-}
-
-}  // namespace
-
-// Byte offsets of the per-CTA shared-memory arrays; every array starts on a
-// 16-byte boundary.  Used by the kernel's carve-up and the host's sizing.
-struct SmemLayout {
-  size_t u0, u1, F, r, z, p, q, d, hm, pinv, cs, code, red, slot, bc, total;
-};
-
-__host__ __device__ inline SmemLayout smem_layout(int dim, int nmax, int kr, bool coef_smem, int nt) {
-  SmemLayout L;
-  size_t o = 0;
-  auto take = [&](size_t bytes) {
-    size_t at = o;
-    o = (o + bytes + 15) & ~(size_t)15;
-    return at;
-  };
-  const size_t n8 = (size_t)nmax * 8, nk = (size_t)nmax * kr;
-  L.u0 = take(n8); L.u1 = take(n8); L.F = take(n8);
-  L.r = take(nk); L.z = take(nk); L.p = take(nk); L.q = take(nk); L.d = take(nk);
-  L.hm = take(nk); L.pinv = take(nk);
-  L.cs = take(coef_smem ? (size_t)n_offsets(dim) * nk : 0);
-  L.code = take((size_t)nmax * 4);
-  L.red = take((size_t)4 * 32 * 8);
-  L.slot = take((size_t)2 * 4 * 16 * 8);
-  L.bc = take(8 * 8);
-  L.total = o;
-  return L;
-}
+cudaError_t launch_solve_cluster_gmg(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
+                                     bool mixed, const ClusterPlan& pl, int n, const double* coef64,
+                                     const float* coef32, double* slab, double* t_act,
+                                     mlmc_sample_info* info, unsigned long long* counters,
+                                     const ClusterGlobal& g, const MGDesc& mg, cudaStream_t st);
 
 // Shared-memory bytes of one CTA.
 size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt) {
   return smem_layout(dim, nmax, mixed ? 4 : 8, coef_smem, nt).total;
 }
 
-template <typename KR, int DIM, int NT, int NPT, bool GM>
-__global__ void __launch_bounds__(NT, 1)
-solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict__ coef64,
-                     const KR* __restrict__ coefK, int H, int coef_smem, double* slab,
-                     double* t_act, mlmc_sample_info* info, unsigned long long* counters,
-                     double* g_u, double* g_F, KR* g_kr, unsigned* g_code) {
-  constexpr int NO = DIM == 3 ? 27 : 9;
-  constexpr int CTR = DIM == 3 ? 13 : 4;
-  cg::cluster_group cl = cg::this_cluster();
-  Band b;
-  b.C = (int)cl.num_blocks();
-  b.rank = (int)cl.block_rank();
-  b.N0 = lv.N[0]; b.N1 = lv.N[1]; b.N2 = lv.N[2];
-  b.rowlen = DIM == 3 ? b.N0 * b.N1 : b.N0;
-  b.nrows = DIM == 3 ? b.N2 : b.N1;
-  b.H = H;
-  const int s = blockIdx.x / b.C;
-  const int N = (int)lv.nodes;
-  if (GM) {
-    // H nodes per CTA, contiguous
-    b.base = min(b.rank * H, N);
-    b.nb = min(H, N - b.base);
-    b.row0 = b.row1 = 0;
-    b.nmax = H;
-  } else {
-    b.row0 = min(b.rank * H, b.nrows);
-    b.row1 = min(b.row0 + H, b.nrows);
-    b.nb = (b.row1 - b.row0) * b.rowlen;
-    b.nmax = H * b.rowlen;
-    b.base = b.row0 * b.rowlen;
-  }
-  const int base = b.base;
-  const int nmax = b.nmax;
-  const int N01 = b.N0 * b.N1;
-  const int tid = threadIdx.x;
-
-  extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(DIM, GM ? 0 : nmax, (int)sizeof(KR), !GM && coef_smem != 0, NT);
-  double* ubuf0 = GM ? g_u + (int64_t)s * 2 * N + base : (double*)(smem + L.u0);
-  double* ubuf1 = GM ? g_u + (int64_t)s * 2 * N + N + base : (double*)(smem + L.u1);
-  double* F = GM ? g_F + (int64_t)s * N + base : (double*)(smem + L.F);
-  KR* const kr0 = GM ? g_kr + (int64_t)s * 7 * N + base : nullptr;
-  KR* r = GM ? kr0 : (KR*)(smem + L.r);
-  KR* z = GM ? kr0 + N : (KR*)(smem + L.z);
-  KR* p = GM ? kr0 + 2 * N : (KR*)(smem + L.p);
-  KR* q = GM ? kr0 + 3 * N : (KR*)(smem + L.q);
-  KR* d = GM ? kr0 + 4 * N : (KR*)(smem + L.d);
-  KR* hm = GM ? kr0 + 5 * N : (KR*)(smem + L.hm);
-  KR* pinv = GM ? kr0 + 6 * N : (KR*)(smem + L.pinv);
-  KR* cs = (KR*)(smem + L.cs);                             // couplings [NO][nmax] if coef_smem
-  double* red = (double*)(smem + L.red);
-  double* slot = (double*)(smem + L.slot);
-  double* bc = (double*)(smem + L.bc);
-  int par = 0;
-
-  const double* c64 = coef64 + (int64_t)s * NO * N;
-  const KR* cKg = coefK + (int64_t)s * NO * N;
-  double* ta = t_act + (int64_t)s * N;
-  double* sl = slab ? slab + (int64_t)s * (lv.m + 1) * N : nullptr;
-  const double dt = lv.dt, inv_dt = 1.0 / lv.dt;
-
-  // Per node: packed coordinates i | j << 11 | k << 22 and, in bit 31, whether
-  // every neighbour lies inside the domain and inside this band (then the
-  // stencil uses constant local offsets).
-  unsigned* code = GM ? g_code + (int64_t)s * N + base : (unsigned*)(smem + L.code);
-  for (int a = tid; a < b.nb; a += NT) {
-    int i, j, k, row;
-    if (GM) {
-      const int A = base + a;
-      i = A % b.N0;
-      j = (A / b.N0) % b.N1;
-      k = A / N01;
-      row = DIM == 3 ? k : j;
-    } else {
-      const int lr = a / b.rowlen, inrow = a - lr * b.rowlen;
-      row = b.row0 + lr;
-      if (DIM == 3) { k = row; j = inrow / b.N0; i = inrow - j * b.N0; }
-      else { k = 0; j = row; i = inrow; }
-    }
-    bool in = i > 0 && i < b.N0 - 1 && j > 0 && j < b.N1 - 1 && (DIM == 2 || (k > 0 && k < b.N2 - 1));
-    bool fast = in && (GM || (row > b.row0 && row < b.row1 - 1));
-    code[a] = (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22) | (fast ? 0x80000000u : 0u);
-  }
-#define CI(c) ((int)((c) & 2047u))
-#define CJ(c) ((int)(((c) >> 11) & 2047u))
-#define CK_(c) ((int)(((c) >> 22) & 511u))
-#define CFAST(c) (((c) & 0x80000000u) != 0u)
-
-  cl.sync();   // every CTA of the cluster is resident before any DSMEM access
-
-  if (!GM && coef_smem)
-    for (int o = 0; o < NO; ++o)
-      for (int a = tid; a < b.nb; a += NT) cs[o * nmax + a] = cKg[(int64_t)o * N + base + a];
-  double sc[3];
-  for (int dd = 0; dd < 3; ++dd) sc[dd] = ph.stim_ps ? ph.stim_ps[3 * s + dd] : ph.stim_c[dd];
-  for (int a = tid; a < b.nb; a += NT) {
-    const unsigned c = code[a];
-    const int A = base + a;
-    double x[3] = {CI(c) * lv.h[0], CJ(c) * lv.h[1], CK_(c) * lv.h[2]};
-    double r2 = 0.0;
-    for (int dd = 0; dd < DIM; ++dd) r2 += (x[dd] - sc[dd]) * (x[dd] - sc[dd]);
-    double v = r2 < ph.stim_r2 ? 1.0 : 0.0;
-    ubuf0[a] = v;
-    ta[A] = v >= 0.5 ? 0.0 : -1.0;
-    if (sl) sl[A] = v;
-  }
-  const View<KR> pv = make_view<GM>(cl, b, p);
-  const View<KR> dv = make_view<GM>(cl, b, d);
-  const View<double> uv0 = make_view<GM>(cl, b, ubuf0);
-  const View<double> uv1 = make_view<GM>(cl, b, ubuf1);
-  const double rtol2 = sp.lin_rtol * sp.lin_rtol;
-
-  int status = MLMC_OK, failed_step = 0;
-  int newton_total = 0, cg_total = 0, trunc_total = 0, halvings = 0, max_newton = 0;
-  for (int step = 1; step <= lv.m; ++step) {
-    double* u = (step & 1) ? ubuf1 : ubuf0;
-    const double* up = (step & 1) ? ubuf0 : ubuf1;
-    const View<double>& uv = (step & 1) ? uv1 : uv0;
-    for (int a = tid; a < b.nb; a += NT) u[a] = up[a];
-    cluster_barrier(cl, b.C);
-    bool conv = false, lin_fail = false;
-    int it;
-    for (it = 1; it <= sp.newton_max; ++it) {
-      // residual, Hessian diagonal and the CG start r = -F, z = P^-1 r, p = z, d = 0
-      KR rz_loc = 0;
-      for (int a = tid; a < b.nb; a += NT) {
-        const unsigned c = code[a];
-        const int A = base + a;
-        auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
-        const double ku = CFAST(c) ? stencil_fast<DIM, double>(u, a, b.N0, N01, c64A)
-                                   : stencil_band<DIM, GM, double>(b, uv, CI(c), CJ(c), CK_(c), c64A);
-        const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c)), uA = u[a];
-        const double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
-        F[a] = f;
-        // Hessian diagonal and Jacobi inverse in the CG's precision (the CG is
-        // the only user); no FP64 division on the per-node path
-        const KR uK = (KR)uA, mK = (KR)mA;
-        const KR rdK = (KR)ph.c * ((KR)(-3.0) * uK * uK + (KR)(2.0 * (1.0 + ph.a)) * uK - (KR)ph.a);
-        const KR hmA = mK * ((KR)inv_dt - rdK);
-        const KR pvv = (KR)1 / fabs(hmA + (KR)c64[(int64_t)CTR * N + A]);
-        const KR rv = (KR)(-f);
-        const KR zv = pvv * rv;
-        hm[a] = hmA;
-        pinv[a] = pvv;
-        r[a] = rv; z[a] = zv; p[a] = zv; d[a] = (KR)0;
-        rz_loc += rv * zv;
-      }
-      {
-        KR v1[1] = {rz_loc};
-        cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
-      }
-      double rz = bc[0];
-      const double rz_stop = rtol2 * rz;
-      int cgi = 0;
-      bool truncated = false;
-      if (rz > 0.0) {
-        bool ok = false;
-        for (cgi = 1; cgi <= sp.lin_max; ++cgi) {
-          KR pq_loc = 0;
-          for (int a = tid; a < b.nb; a += NT) {
-            const unsigned c = code[a];
-            const int A = base + a;
-            KR hp;
-            if (!GM && coef_smem) {
-              auto cf = [=](int o) { return cs[o * nmax + a]; };
-              hp = CFAST(c) ? stencil_fast<DIM, KR>(p, a, b.N0, N01, cf)
-                            : stencil_band<DIM, GM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
-            } else {
-              auto cf = [=](int o) { return cKg[(int64_t)o * N + A]; };
-              hp = CFAST(c) ? stencil_fast<DIM, KR>(p, a, b.N0, N01, cf)
-                            : stencil_band<DIM, GM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
-            }
-            const KR pa = p[a];
-            const KR qv = hp + hm[a] * pa;
-            q[a] = qv;
-            pq_loc += pa * qv;
-          }
-          const double rzc = rz;
-          {
-            KR v1[1] = {pq_loc};
-            cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, [=](double* o) {
-              o[1] = o[0] > 0.0 ? (double)((KR)rzc / (KR)o[0]) : 0.0;
-            });
-          }
-          const double pq = bc[0];
-          if (pq <= 0.0) {
-            truncated = true;
-            if (cgi == 1)
-              for (int a = tid; a < b.nb; a += NT) d[a] = z[a];
-            ok = true;
-            break;
-          }
-          const KR alpha = (KR)bc[1];
-          KR rzn_loc = 0;
-          for (int a = tid; a < b.nb; a += NT) {
-            d[a] += alpha * p[a];
-            const KR rv = r[a] - alpha * q[a];
-            const KR zv = pinv[a] * rv;
-            r[a] = rv;
-            z[a] = zv;
-            rzn_loc += rv * zv;
-          }
-          {
-            KR v1[1] = {rzn_loc};
-            cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, [=](double* o) {
-              o[1] = (double)((KR)o[0] / (KR)rzc);
-              o[2] = o[0] <= rz_stop ? 1.0 : 0.0;
-            });
-          }
-          const double rz_new = bc[0];
-          if (bc[2] != 0.0) { ok = true; break; }
-          const KR beta = (KR)bc[1];
-          for (int a = tid; a < b.nb; a += NT) p[a] = z[a] + beta * p[a];
-          cluster_barrier(cl, b.C);
-          rz = rz_new;
-        }
-        if (!ok) { lin_fail = true; cgi = sp.lin_max; }
-      }
-      cg_total += cgi;
-      trunc_total += truncated ? 1 : 0;
-      if (lin_fail) break;
-      KR dm_loc = 0;
-      for (int a = tid; a < b.nb; a += NT) dm_loc = fmax(dm_loc, fabs(d[a]));   // exact in KR
-      {
-        KR v1[1] = {dm_loc};
-        cluster_reduce<NT, KR, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
-      }
-      const double dmax = bc[0];
-      double alpha = 1.0;
-      if (dmax > sp.step_max) {
-        // max-norm trust region: clip every component, or scale the whole
-        // direction if the clipped one is not a descent direction
-        const KR lim = (KR)sp.step_max;
-        double g1[1] = {0.0};
-        for (int a = tid; a < b.nb; a += NT) g1[0] += F[a] * (double)fmin(fmax(d[a], -lim), lim);
-        cluster_reduce<NT, double, 1>(g1, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
-        if (bc[0] < 0.0) {
-          for (int a = tid; a < b.nb; a += NT) d[a] = fmin(fmax(d[a], -lim), lim);
-          cluster_barrier(cl, b.C);
-        } else {
-          alpha = sp.step_max / dmax;
-        }
-      }
-      if (dmax > sp.newton_tol && dmax > sp.ls_full_step) {
-        // The step energy is a quartic polynomial in the step length (R is a
-        // quartic), so for every trial length al
-        //   E(u + al d) - E(u) = al g.d + al^2 d.Hd / 2 - al^3 P3 - al^4 P4,
-        //   P3 = sum_i m_i r2(u_i) d_i^3 / 6,  P4 = sum_i m_i r3 d_i^4 / 24,
-        // with r2 = r'' = c(2(1+a) - 6u) and r3 = r''' = -6c; one pass over the
-        // nodes gives the four sums and thread 0 runs every Armijo test.
-        double v4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int a = tid; a < b.nb; a += NT) {
-          const unsigned c = code[a];
-          const int A = base + a;
-          auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
-          const double kd = CFAST(c) ? stencil_fast<DIM, double>(d, a, b.N0, N01, c64A)
-                                     : stencil_band<DIM, GM, double>(b, dv, CI(c), CJ(c), CK_(c), c64A);
-          const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c));
-          const double uA = u[a], da = (double)d[a], d2 = da * da;
-          const double r1 = ph.c * (-3.0 * uA * uA + 2.0 * (1.0 + ph.a) * uA - ph.a);
-          const double r2 = ph.c * (2.0 * (1.0 + ph.a) - 6.0 * uA);
-          v4[0] += F[a] * da;
-          v4[1] += mA * (inv_dt - r1) * d2 + da * kd;
-          v4[2] += mA * r2 * d2 * da;
-          v4[3] += mA * d2 * d2;
-        }
-        const double alpha0 = alpha, cc = ph.c;
-        cluster_reduce<NT, double, 4>(v4, 0, red, slot, bc, par, cl, b.C, b.rank,
-                                      [=](double* o) {
-                                        const double gd = o[0], dHd = o[1];
-                                        const double P3 = o[2] / 6.0, P4 = -6.0 * cc * o[3] / 24.0;
-                                        double al = alpha0;
-                                        int h = 0;
-                                        for (; h < 40; ++h) {
-                                          const double dE = al * gd + 0.5 * al * al * dHd -
-                                                            al * al * al * P3 - al * al * al * al * P4;
-                                          if (dE <= 1e-4 * al * gd) break;
-                                          al *= 0.5;
-                                        }
-                                        o[4] = al;
-                                        o[5] = (double)h;
-                                      });
-        alpha = bc[4];
-        halvings += (int)bc[5];
-      }
-      for (int a = tid; a < b.nb; a += NT) u[a] += alpha * (double)d[a];
-      cluster_barrier(cl, b.C);
-      if (dmax <= sp.newton_tol) { conv = true; break; }
-    }
-    int used = it > sp.newton_max ? sp.newton_max : it;
-    newton_total += used;
-    max_newton = used > max_newton ? used : max_newton;
-    if (!conv) { status = MLMC_ERR_NOT_CONVERGED; failed_step = step; break; }
-    for (int a = tid; a < b.nb; a += NT) {
-      const int A = base + a;
-      if (ta[A] < 0.0 && u[a] >= 0.5) {
-        double uo = up[a];
-        ta[A] = (double)(step - 1) * dt + dt * (0.5 - uo) / (u[a] - uo);
-      }
-      if (sl) sl[(int64_t)step * N + A] = u[a];
-    }
-  }
-#undef CI
-#undef CJ
-#undef CK_
-#undef CFAST
-  for (int a = tid; a < b.nb; a += NT)
-    if (ta[base + a] < 0.0) ta[base + a] = lv.T;
-  if (b.rank == 0 && tid == 0) {
-    if (counters) {
-      if (status != MLMC_OK) atomicAdd(counters, 1ull);
-      atomicAdd(counters + 1, (unsigned long long)cg_total * (unsigned long long)N);
-      atomicAdd(counters + 2, (unsigned long long)newton_total * (unsigned long long)N);
-      atomicAdd(counters + 3, (unsigned long long)trunc_total);
-      atomicAdd(counters + 4, (unsigned long long)halvings);
-      if (sizeof(KR) == 8) atomicAdd(counters + 5, (unsigned long long)cg_total * (unsigned long long)N);
-    }
-    if (info) {
-      mlmc_sample_info o;
-      o.status = status; o.failed_step = failed_step; o.newton_iters = newton_total;
-      o.cg_iters = cg_total; o.truncations = trunc_total; o.halvings = halvings;
-      o.max_newton = max_newton; o.pad = 0;
-      info[s] = o;
-    }
-  }
-  cl.sync();   // no CTA leaves while a neighbour may still read its shared memory
-}
 
 // Launch plan: the smallest cluster whose bands fit the shared memory (or the
 // requested size want_C), and the block size.  Returns false when it does not
@@ -584,54 +55,17 @@ bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan
   return false;
 }
 
-template <typename KR, int DIM, bool GM>
-static cudaError_t set_attrs(const ClusterPlan& pl) {
-  auto kern = solve_cluster_kernel<KR, DIM, 512, 5, GM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-  if (e == cudaSuccess && pl.C > 8)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  return e;
-}
-
-static cudaLaunchConfig_t launch_cfg(const ClusterPlan& pl, int n, cudaStream_t st,
-                                     cudaLaunchAttribute* at) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(n * pl.C));
-  cfg.blockDim = dim3(512);
-  cfg.dynamicSmemBytes = pl.smem;
-  cfg.stream = st;
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = pl.C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cfg;
-}
-
-template <typename KR, int DIM, bool GM>
-static cudaError_t launch_one(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
-                              const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
-                              double* slab, double* t_act, mlmc_sample_info* info,
-                              unsigned long long* counters, const ClusterGlobal& g,
-                              cudaStream_t st) {
-  cudaError_t e = set_attrs<KR, DIM, GM>(pl);
-  if (e != cudaSuccess) return e;
-  cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = launch_cfg(pl, n, st, at);
-  return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<KR, DIM, 512, 5, GM>, lv, ph, sp, coef64, coefK,
-                            pl.H, pl.coef_smem ? 1 : 0, slab, t_act, info, counters, g.u, g.F,
-                            (KR*)g.kr, g.code);
-}
-
 template <typename KR, int DIM>
 static cudaError_t launch_nt(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                              const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
                              double* slab, double* t_act, mlmc_sample_info* info,
-                             unsigned long long* counters, const ClusterGlobal& g, cudaStream_t st) {
+                             unsigned long long* counters, const ClusterGlobal& g,
+                             const MGDesc& mg, cudaStream_t st) {
   if (pl.gm)
-    return launch_one<KR, DIM, true>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info, counters, g, st);
-  return launch_one<KR, DIM, false>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info, counters, g, st);
+    return launch_one<KR, DIM, true, false>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info,
+                                            counters, g, mg, st);
+  return launch_one<KR, DIM, false, false>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info,
+                                           counters, g, mg, st);
 }
 
 template <typename KR, int DIM>
@@ -645,8 +79,8 @@ static cudaError_t max_clusters_one(const ClusterPlan& pl, int* count) {
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t cfg = launch_cfg(pl, 1, nullptr, at);
-  return pl.gm ? cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, true>, &cfg)
-               : cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, false>, &cfg);
+  return pl.gm ? cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, true, false>, &cfg)
+               : cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, false, false>, &cfg);
 }
 
 cudaError_t preload_solve_cluster(const LevelDesc& lv, bool mixed, const ClusterPlan& pl) {
@@ -663,17 +97,77 @@ cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const S
                                  bool mixed, const ClusterPlan& pl, int n, const double* coef64,
                                  const float* coef32, double* slab, double* t_act,
                                  mlmc_sample_info* info, unsigned long long* counters,
-                                 const ClusterGlobal& g, cudaStream_t st) {
+                                 const ClusterGlobal& g, const MGDesc& mg, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   if (pl.gm && (!g.u || !g.F || !g.kr || !g.code)) return cudaErrorInvalidValue;
+  if (pl.gm && mg.G > 0) {
+    if (!g.mg || mg.nu < 1 || mg.coarse_sweeps < 1 || mg.G > MG_MAX_LEVELS) return cudaErrorInvalidValue;
+    return launch_solve_cluster_gmg(lv, ph, sp, mixed, pl, n, coef64, coef32, slab, t_act, info,
+                                    counters, g, mg, st);
+  }
   if (mixed) {
     if (lv.dim == 3)
-      return launch_nt<float, 3>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, st);
-    return launch_nt<float, 2>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, st);
+      return launch_nt<float, 3>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, mg, st);
+    return launch_nt<float, 2>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, mg, st);
   }
   if (lv.dim == 3)
-    return launch_nt<double, 3>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, st);
-  return launch_nt<double, 2>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, st);
+    return launch_nt<double, 3>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, mg, st);
+  return launch_nt<double, 2>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, mg, st);
+}
+
+// Multigrid hierarchy of grid lv (see MGDesc): level 0 is lv itself; every
+// axis with an even cell count >= 2 is halved per level while the grid has
+// more than 512 nodes.  Arrays are padded to 64 elements.
+void mg_hierarchy(const LevelDesc& lv, int nu, int coarse_sweeps, MGDesc* mg) {
+  *mg = MGDesc();
+  mg->nu = nu;
+  mg->coarse_sweeps = coarse_sweeps;
+  const int NO = n_offsets(lv.dim);
+  auto pad = [](int64_t x) { return (x + 63) & ~(int64_t)63; };
+  int n[3] = {lv.n[0], lv.n[1], lv.n[2]};
+  int64_t off = 0;
+  int G = 0;
+  while (G < MG_MAX_LEVELS) {
+    MGLevel& L = mg->l[G];
+    int64_t nodes = 1;
+    for (int d = 0; d < 3; ++d) {
+      L.n[d] = d < lv.dim ? n[d] : 1;
+      L.N[d] = d < lv.dim ? n[d] + 1 : 1;
+      nodes *= L.N[d];
+    }
+    L.nodes = (int)nodes;
+    const int64_t np = pad(nodes);
+    if (G == 0) {
+      L.K = L.d = L.inv = L.b = -1;
+      L.ks = off; off += np;
+      L.xa = off; off += np;
+      L.xb = off; off += np;
+      L.t = off; off += np;
+    } else {
+      L.K = off; off += (int64_t)NO * np;
+      L.ks = off; off += np;
+      L.d = off; off += np;
+      L.inv = off; off += np;
+      L.xa = off; off += np;
+      L.xb = off; off += np;
+      L.b = off; off += np;
+      L.t = off; off += np;
+    }
+    ++G;
+    bool any = false;
+    for (int d = 0; d < 3; ++d) {
+      L.cz[d] = d < lv.dim && n[d] >= 2 && n[d] % 2 == 0;
+      any = any || L.cz[d];
+    }
+    if (!any || nodes <= 512 || G == MG_MAX_LEVELS) {
+      for (int d = 0; d < 3; ++d) L.cz[d] = 0;
+      break;
+    }
+    for (int d = 0; d < 3; ++d)
+      if (L.cz[d]) n[d] /= 2;
+  }
+  mg->G = G;
+  mg->per_sample = pad(off);
 }
 
 }  // namespace mlmc

@@ -37,7 +37,8 @@ def test_every_declared_symbol_is_exported(lib):
 def test_invalid_configs_rejected_on_host(lib):
     cfg = B.make_config(W.MC2D_32)
     for field, bad in [("dim", 4), ("n_levels", 0), ("n_levels", 9), ("m0", 0), ("kl_modes", 0),
-                       ("precision", 7), ("newton_max", 0), ("lin_rtol", 0.0), ("kl_ell", -1.0)]:
+                       ("precision", 7), ("newton_max", 0), ("lin_rtol", 0.0), ("kl_ell", -1.0),
+                       ("precond", 2), ("mg_nu", 9), ("mg_nu", -1), ("mg_coarse_sweeps", 65)]:
         c = B.make_config(W.MC2D_32)
         setattr(c, field, bad)
         h = C.c_void_p()
