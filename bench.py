@@ -52,11 +52,21 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch each estimate's kernels directly instead of as one CUDA graph")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the time-to-eps run and the serving run (reported beside the step time)")
     ap.add_argument("--profile-case", type=int, default=None, metavar="LEVEL",
                     help="run one small solve of LEVEL (2 samples, after one warm-up solve) for "
                          "an ncu capture of the solve kernel, instead of the benchmark")
+    ap.add_argument("--profile-workload", default="2d", choices=["2d", "3d"],
+                    help="--profile-case on the 3-level 2D workload or the 4-level 3D slab")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="--profile-case: only the first STEPS time steps of the level (same dt)")
+    ap.add_argument("--profile-precond", default="jacobi", choices=["jacobi", "gmg"])
+    ap.add_argument("--profile-kl", type=int, default=None, metavar="LEVEL",
+                    help="run the tensor-core KL synthesis of LEVEL of the 3D slab twice for 256 "
+                         "samples (the second launch is the one to capture), instead of the benchmark")
     return ap.parse_args()
 
 
@@ -194,10 +204,13 @@ def run_ours(args, w):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prec = B.MLMC_PREC_MIXED if args.precision == "mixed" else B.MLMC_PREC_FP64
-    ctx = B.Context(B.make_config(w, prec))
+    graph = not args.no_graph
+    ctx = B.Context(B.make_config(w, prec, use_graph=graph))
     seed = 1 + rank      # disjoint streams per rank: each rank runs its own estimate
     batch = max(w["N"])
-    stream = torch.cuda.current_stream()
+    # a side stream: the legacy default stream cannot be captured into a graph
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -264,6 +277,7 @@ def run_ours(args, w):
         "config": {"workload": w["name"], "N_l": w["N"], "grids": "32^2/64^2/128^2",
                    "steps_per_level": [64, 128, 256], "kl_modes": w["M"],
                    "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+                   "launch": "one CUDA graph per estimate" if graph else "direct launches",
                    "rmse_achieved": statistics.mean(rmse),
                    "parallelism": "one thread-block cluster per sample; levels on concurrent streams"},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * L,
@@ -302,7 +316,7 @@ def run_extras(w, B, prec, seed):
     from paper_1911_06066_gb300 import serving as S
 
     eps = 1e-3 * w["T"]
-    ctx = B.Context(B.make_config(w, prec))
+    ctx = B.Context(B.make_config(w, prec, use_graph=True))
     ctx.run([64, 16, 4], seed=seed + 100, batch=64)          # warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -350,30 +364,69 @@ def run_extras(w, B, prec, seed):
 
 def run_profile_case(args, w):
     """Two samples of one level of the benchmark workload through mlmc_solve:
-    launch 1 is a warm-up, launch 2 the one to capture (ncu -s 1 -c 1)."""
+    launch 1 is a warm-up, launch 2 the one to capture (ncu -s 1 -c 1).
+    --profile-steps S keeps the level's time step and runs only its first S
+    steps (a shorter end time), so that a capture of a large level ends soon."""
     import torch
     from __graft_entry__ import build
     build()
     from paper_1911_06066_gb300 import binding as B
-    prec = B.MLMC_PREC_MIXED if args.precision == "mixed" else B.MLMC_PREC_FP64
-    ctx = B.Context(B.make_config(w, prec))
     level = args.profile_case
+    if args.profile_steps:
+        m_full = w["m0"] * 2 ** level
+        steps = args.profile_steps
+        if steps % (2 ** level) or steps > m_full:
+            raise SystemExit("--profile-steps must be a multiple of 2^level, at most the level's steps")
+        w = dict(w, m0=steps // 2 ** level, T=w["T"] * steps / m_full)
+    prec = B.MLMC_PREC_MIXED if args.precision == "mixed" else B.MLMC_PREC_FP64
+    pc = B.MLMC_PRECOND_GMG if args.profile_precond == "gmg" else B.MLMC_PRECOND_JACOBI
+    ctx = B.Context(B.make_config(w, prec, precond=pc))
     Z = ctx.kl_field(level, ctx.xi(0, level, torch.arange(2)))
     ctx.solve(level, Z[:1])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, _, info = ctx.solve(level, Z)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": level, "precision": args.precision, "samples": 2,
+    print(json.dumps({"profile_case": level, "workload": w["name"], "steps": w["m0"] * 2 ** level,
+                      "precision": args.precision, "precond": args.profile_precond, "samples": 2,
                       "seconds": time.perf_counter() - t0, "info": B.info_dicts(info)}))
+
+
+def run_profile_kl(args):
+    """The tensor-core KL synthesis of one level of the 3D slab for 256 samples,
+    twice: launch 1 warms up, launch 2 is the one to capture (ncu -s 1 -c 1)."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_1911_06066_gb300 import binding as B
+    from paper_1911_06066_gb300 import workloads as W
+    w = W.SLAB3D_4LVL
+    level = args.profile_kl
+    ctx = B.Context(B.make_config(w, B.MLMC_PREC_MIXED))
+    xi = ctx.xi(0, level, torch.arange(256))
+    ctx.kl_field_tc(level, xi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    Z = ctx.kl_field_tc(level, xi)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, cells, _ = ctx.level_info(level)
+    flops = 2.0 * 3 * cells * 256 * ((w["M"] + 31) // 32 * 32)
+    print(json.dumps({"profile_kl": level, "cells": cells, "samples": 256, "modes": w["M"],
+                      "ms": ms, "tensor_tflops_3xtf32": flops / ms * 1e-9,
+                      "z_bytes_gbs": cells * 256 * 8 / ms * 1e-6, "z_absmax": float(Z.abs().max())}))
 
 
 def main():
     args = parse()
     from paper_1911_06066_gb300 import workloads as W
     w = W.MLMC2D_3LVL
-    if args.profile_case is not None:
-        run_profile_case(args, w)
+    if args.profile_kl is not None:
+        run_profile_kl(args)
+    elif args.profile_case is not None:
+        run_profile_case(args, W.SLAB3D_4LVL if args.profile_workload == "3d" else w)
     elif args.impl == "reference":
         run_reference(args, w)
     else:

@@ -87,6 +87,13 @@ typedef struct {
                             correction, 0..8 (0 selects the default 2)                   */
   int mg_coarse_sweeps;  /* MLMC_PRECOND_GMG: smoothing sweeps on the coarsest grid, 0..64
                             (0 selects the default 8)                                    */
+  int use_graph;         /* nonzero: mlmc_run / mlmc_run_more / mlmc_run_to_rmse capture
+                            their whole multi-stream schedule of one call (every batch of
+                            every level) into a CUDA graph and launch it as one unit; the
+                            instantiated graph is kept and updated in place when the next
+                            call has the same shape.  Ignored on the legacy default stream
+                            (stream NULL), which cannot be captured.  Results are
+                            identical to the direct launches.                            */
 } mlmc_config;
 
 /* Row a7 -- preconditioner of the Newton steps' CG (the paper's Krylov solver

@@ -31,7 +31,7 @@ class mlmc_config(C.Structure):
                 ("precision", C.c_int), ("newton_tol", C.c_double), ("newton_max", C.c_int),
                 ("lin_rtol", C.c_double), ("lin_max", C.c_int), ("solver", C.c_int),
                 ("mixed_cdr_max", C.c_double), ("cluster_size", C.c_int), ("precond", C.c_int),
-                ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int)]
+                ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int), ("use_graph", C.c_int)]
 
 
 MLMC_SOLVER_AUTO, MLMC_SOLVER_BLOCK, MLMC_SOLVER_CLUSTER = 0, 1, 2
@@ -189,7 +189,8 @@ class State:
 
 def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, lin_rtol=1e-12,
                 lin_max=5000, levels=None, solver=MLMC_SOLVER_AUTO, mixed_cdr_max=0.0,
-                cluster_size=0, precond=MLMC_PRECOND_JACOBI, mg_nu=0, mg_coarse_sweeps=0):
+                cluster_size=0, precond=MLMC_PRECOND_JACOBI, mg_nu=0, mg_coarse_sweeps=0,
+                use_graph=False):
     """mlmc_config from a workload dictionary (see workloads.py)."""
     c = mlmc_config()
     c.dim = w["dim"]
@@ -210,6 +211,7 @@ def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, 
     c.mixed_cdr_max = mixed_cdr_max
     c.cluster_size = cluster_size
     c.precond, c.mg_nu, c.mg_coarse_sweeps = precond, mg_nu, mg_coarse_sweeps
+    c.use_graph = 1 if use_graph else 0
     return c
 
 

@@ -230,6 +230,7 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
       return cleanup_fail(e, "cudaStreamCreate");
   if ((e = cudaStreamCreateWithFlags(&ctx->aux_pub, cudaStreamNonBlocking)) != cudaSuccess)
     return cleanup_fail(e, "cudaStreamCreate");
+  if ((e = preload_kl_tc()) != cudaSuccess) return cleanup_fail(e, "cudaFuncSetAttribute");
   *out = ctx;
   return MLMC_OK;
 }
@@ -244,6 +245,7 @@ extern "C" void mlmc_destroy(mlmc_ctx* ctx) {
   cudaFree(ctx->d_N);
   cudaFree(ctx->d_est);
   cudaFree(ctx->d_cnt);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
   for (cudaEvent_t ev : ctx->sync_pool) cudaEventDestroy(ev);
   for (int i = 0; i < 2 * MLMC_MAX_LEVELS; ++i)
@@ -393,7 +395,7 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     e0 = ctx->ev_pool[ctx->ev_used++];
     e1 = ctx->ev_pool[ctx->ev_used++];
     ctx->ev_level.push_back(ctx->prof_level);
-    CK(ctx, cudaEventRecord(e0, st));
+    CK(ctx, cudaEventRecordWithFlags(e0, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
   SolverParams sp = ctx->sp;
   sp.lin_rtol = mixed ? fmax(ctx->cfg.lin_rtol, 1e-5) : ctx->cfg.lin_rtol;
@@ -414,7 +416,8 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     CK(ctx, launch_solve(lv, ph, sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
                          (double*)(ws + w.F), (double*)(ws + w.Ku), (double*)(ws + w.Kd),
                          (void*)(ws + w.kr), t_act, info, ctx->d_cnt, st));
-  if (ctx->prof) CK(ctx, cudaEventRecord(e1, st));
+  if (ctx->prof)
+    CK(ctx, cudaEventRecordWithFlags(e1, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   ctx->launches += 2;
   return MLMC_OK;
 }
@@ -689,11 +692,83 @@ extern "C" mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, const int64
 // concurrently.  Ordered after the work already on st; st waits for it all.
 // lvl_ms (host [levels] or NULL) receives each level's summed solve-kernel
 // time in ms (the solves of its pairs, fine and coarse).
+static mlmc_status enqueue_levels(mlmc_ctx* ctx, const int64_t* first_id, const int64_t* count,
+                                  uint64_t seed, int batch, char* ws, cudaStream_t st);
+
+// With cfg.use_graph the schedule of one call is captured from `st` (every
+// context stream joins the capture through the fork / join events) and
+// launched as one CUDA graph; the executable graph is updated in place when
+// the next call has the same topology (other seeds, ids or workspace), else
+// instantiated anew.
 static mlmc_status run_levels(mlmc_ctx* ctx, const int64_t* first_id, const int64_t* count,
                               uint64_t seed, int batch, char* ws, cudaStream_t st, double* lvl_ms) {
   const int L = ctx->cfg.n_levels;
   mlmc_status r;
   const size_t ev0 = ctx->ev_used;
+  const bool graph = ctx->cfg.use_graph != 0 && st != nullptr;
+  if (graph) {
+    // kernel attributes are set before the capture
+    for (int l = 0; l < L; ++l) {
+      for (int lv = l; lv >= 0 && lv >= l - 1; --lv) {
+        const LevelDesc& d = ctx->lv[lv];
+        const bool mx = level_mixed(ctx->cfg, d);
+        ClusterPlan pl;
+        if (choose_plan(ctx, d, mx, lv, &pl)) CK(ctx, preload_solve_cluster(d, mx, pl));
+        else CK(ctx, preload_solve(d, mx));
+      }
+    }
+    CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    ctx->capturing = true;
+  }
+  r = enqueue_levels(ctx, first_id, count, seed, batch, ws, st);
+  if (graph) {
+    ctx->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (r != MLMC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    if (ctx->graph_exec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(ctx->graph_exec, g, &info) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+      }
+    }
+    if (!ctx->graph_exec) {
+      e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        ctx->graph_exec = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+      }
+    }
+    cudaGraphDestroy(g);
+    CK(ctx, cudaGraphLaunch(ctx->graph_exec, st));
+    ctx->graph_runs += 1;
+  } else if (r != MLMC_OK) {
+    return r;
+  }
+  if (lvl_ms) {
+    CK(ctx, cudaStreamSynchronize(st));
+    for (int l = 0; l < L; ++l) lvl_ms[l] = 0.0;
+    for (size_t i = ev0; i + 1 < ctx->ev_used; i += 2) {
+      float ms = 0.f;
+      CK(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+      lvl_ms[ctx->ev_level[i / 2]] += ms;
+    }
+  }
+  return MLMC_OK;
+}
+
+// The launches of run_levels: every level on its own pair of context streams.
+static mlmc_status enqueue_levels(mlmc_ctx* ctx, const int64_t* first_id, const int64_t* count,
+                                  uint64_t seed, int batch, char* ws, cudaStream_t st) {
+  const int L = ctx->cfg.n_levels;
+  mlmc_status r;
   ctx->prof = true;
   struct ProfOff { mlmc_ctx* c; ~ProfOff() { c->prof = false; } } prof_off{ctx};
   char* p = ws;
@@ -718,15 +793,6 @@ static mlmc_status run_levels(mlmc_ctx* ctx, const int64_t* first_id, const int6
       if ((r = mlmc_accumulate(ctx, l, y, y2, nb, sf)) != MLMC_OK) return r;
     }
     if ((r = order_after(ctx, sf, st)) != MLMC_OK) return r;
-  }
-  if (lvl_ms) {
-    CK(ctx, cudaStreamSynchronize(st));
-    for (int l = 0; l < L; ++l) lvl_ms[l] = 0.0;
-    for (size_t i = ev0; i + 1 < ctx->ev_used; i += 2) {
-      float ms = 0.f;
-      CK(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
-      lvl_ms[ctx->ev_level[i / 2]] += ms;
-    }
   }
   return MLMC_OK;
 }

@@ -38,6 +38,12 @@ struct mlmc_ctx {
   // cluster that holds a sample, C > 0 = clusters of C CTAs, -1 = the
   // block-per-sample kernel
   int tuned_C[MLMC_MAX_LEVELS] = {};
+  // CUDA-graph form of the run schedule (cfg.use_graph): true while a run's
+  // launches are being captured; the instantiated graph of the last run, kept
+  // for in-place updates; how many runs were launched as a graph
+  bool capturing = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  long graph_runs = 0;
   std::string err;
 };
 

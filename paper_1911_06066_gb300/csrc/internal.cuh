@@ -119,6 +119,7 @@ cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_la
                                const double* phi_x, const double* phi_y, const double* phi_z,
                                const double* xi, int n, double* Z, unsigned long long* err,
                                cudaStream_t st);
+cudaError_t preload_kl_tc();
 cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,
                             double* coef64, float* coef32, cudaStream_t st);
 cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,

@@ -258,8 +258,9 @@ kl_field_tc_kernel(LevelDesc lv, int M, int nt, const double* __restrict__ sqrt_
     }
   } else if (tid == 0) {
     atomicAdd(err, 1ull);
-    // bounded wait for the MMAs already issued before the memory is freed
-    mbar_wait(bar, phase);
+    // bounded wait for the MMAs already issued (the commit whose wait ran out;
+    // phase was toggled after it) before the tensor memory is freed
+    mbar_wait(bar, phase ^ 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -271,6 +272,13 @@ kl_field_tc_kernel(LevelDesc lv, int M, int nt, const double* __restrict__ sqrt_
 
 size_t kl_tc_smem_bytes(int nt) { return tc_smem(nt).total + 1024; }
 
+// Allows the largest tile's shared memory on the current device (once per
+// context, before any launch or stream capture).
+cudaError_t preload_kl_tc() {
+  return cudaFuncSetAttribute(kl_field_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kl_tc_smem_bytes(256));
+}
+
 cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
                                const double* phi_x, const double* phi_y, const double* phi_z,
                                const double* xi, int n, double* Z, unsigned long long* err,
@@ -279,10 +287,7 @@ cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_la
   // samples per tile: the batch rounded up to 32, at most 256
   int nt = ((n + 31) / 32) * 32;
   if (nt > 256) nt = 256;
-  const size_t smem = kl_tc_smem_bytes(nt);
-  cudaError_t e = cudaFuncSetAttribute(kl_field_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
+  const size_t smem = kl_tc_smem_bytes(nt);   // within the limit set by preload_kl_tc
   const int64_t tiles = (lv.cells + TC_M - 1) / TC_M;
   if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
   dim3 grid((unsigned)tiles, (unsigned)((n + nt - 1) / nt));

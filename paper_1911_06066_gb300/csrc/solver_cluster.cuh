@@ -187,6 +187,21 @@ struct NoPost {
   __device__ void operator()(double*) const {}
 };
 
+// Packed coordinates and interior flag of node A (the per-node code of the
+// kernel) computed from the index, for the global-memory layout: the hot
+// passes then issue their stencil loads without first waiting for a load of
+// the code.
+template <int DIM>
+__device__ __forceinline__ unsigned gm_code(const Band& b, int A) {
+  const int jk = A / b.N0;
+  const int i = A - jk * b.N0;
+  const int k = jk / b.N1;
+  const int j = jk - k * b.N1;
+  const bool in = i > 0 && i < b.N0 - 1 && j > 0 && j < b.N1 - 1 &&
+                  (DIM == 2 || (k > 0 && k < b.N2 - 1));
+  return (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22) | (in ? 0x80000000u : 0u);
+}
+
 __device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl, int C) {
   if (C == 1) __syncthreads(); else cl.sync();
 }
@@ -349,9 +364,16 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     int it;
     for (it = 1; it <= sp.newton_max; ++it) {
       // residual, Hessian diagonal and the CG start r = -F, z = P^-1 r, p = z, d = 0
+      // FP32 CG: the right-hand side is scaled by a power of two sigma with
+      // max|F| sigma in [1, 2), and d by 1/sigma after the solve.  Both are
+      // exact, so this changes nothing except that the CG's products stay in
+      // FP32's normal range: on fine 3D grids (lumped mass ~ h^3) the late
+      // Newton residuals are ~1e-18 and the CG's r.z fell below 1e-38.
+      constexpr bool SCALE = sizeof(KR) == 4;
+      double fmax_loc = 0.0;
       KR rz_loc = 0;
       for (int a = tid; a < b.nb; a += NT) {
-        const unsigned c = code[a];
+        const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
         const int A = base + a;
         auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
         const double ku = CFAST(c) ? stencil_fast<DIM, double>(u, a, b.N0, N01, c64A)
@@ -359,24 +381,40 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c)), uA = u[a];
         const double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
         F[a] = f;
+        fmax_loc = fmax(fmax_loc, fabs(f));
         // Hessian diagonal and Jacobi inverse in the CG's precision (the CG is
         // the only user); no FP64 division on the per-node path
         const KR uK = (KR)uA, mK = (KR)mA;
         const KR rdK = (KR)ph.c * ((KR)(-3.0) * uK * uK + (KR)(2.0 * (1.0 + ph.a)) * uK - (KR)ph.a);
         const KR hmA = mK * ((KR)inv_dt - rdK);
-        const KR rv = (KR)(-f);
         hm[a] = hmA;
-        r[a] = rv;
         d[a] = (KR)0;
-        if (MG) {
-          // l1-Jacobi inverse of the level-0 smoother: 1 / (|hm| + sum_o |K_o|)
-          pinv[a] = (KR)1 / (fabs(hmA) + mgb[mg.l[0].ks + A]);
-        } else {
-          const KR pvv = (KR)1 / fabs(hmA + (KR)c64[(int64_t)CTR * N + A]);
-          const KR zv = pvv * rv;
-          pinv[a] = pvv;
-          z[a] = zv; p[a] = zv;
-          rz_loc += rv * zv;
+        const KR pvv = MG ? (KR)1 / (fabs(hmA) + mgb[mg.l[0].ks + A])   // l1-Jacobi (V-cycle smoother)
+                          : (KR)1 / fabs(hmA + (KR)c64[(int64_t)CTR * N + A]);
+        pinv[a] = pvv;
+        if (!SCALE) {
+          const KR rv = (KR)(-f);
+          r[a] = rv;
+          if (!MG) {
+            const KR zv = pvv * rv;
+            z[a] = zv; p[a] = zv;
+            rz_loc += rv * zv;
+          }
+        }
+      }
+      double sigma = 1.0;
+      if (SCALE) {
+        double v1[1] = {fmax_loc};
+        cluster_reduce<NT, double, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+        if (bc[0] > 0.0) sigma = ldexp(1.0, -ilogb(bc[0]));
+        for (int a = tid; a < b.nb; a += NT) {
+          const KR rv = (KR)(-F[a] * sigma);
+          r[a] = rv;
+          if (!MG) {
+            const KR zv = pinv[a] * rv;
+            z[a] = zv; p[a] = zv;
+            rz_loc += rv * zv;
+          }
         }
       }
       if (MG) {
@@ -403,7 +441,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         for (cgi = 1; cgi <= sp.lin_max; ++cgi) {
           KR pq_loc = 0;
           for (int a = tid; a < b.nb; a += NT) {
-            const unsigned c = code[a];
+            const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
             const int A = base + a;
             KR hp;
             if (!GM && coef_smem) {
@@ -475,6 +513,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       cg_total += cgi;
       trunc_total += truncated ? 1 : 0;
       if (lin_fail) break;
+      if (SCALE && sigma != 1.0) {
+        const KR inv_sigma = (KR)(1.0 / sigma);   // a power of two: exact
+        for (int a = tid; a < b.nb; a += NT) d[a] *= inv_sigma;
+      }
       KR dm_loc = 0;
       for (int a = tid; a < b.nb; a += NT) dm_loc = fmax(dm_loc, fabs(d[a]));   // exact in KR
       {
@@ -506,7 +548,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         // nodes gives the four sums and thread 0 runs every Armijo test.
         double v4[4] = {0.0, 0.0, 0.0, 0.0};
         for (int a = tid; a < b.nb; a += NT) {
-          const unsigned c = code[a];
+          const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
           const int A = base + a;
           auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
           const double kd = CFAST(c) ? stencil_fast<DIM, double>(d, a, b.N0, N01, c64A)
