@@ -173,14 +173,17 @@ mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi, int n, dou
  * dense contraction (cells x modes) . (modes x samples) on the tensor cores
  * (tcgen05 kind::tf32, accumulators in tensor memory) with the three-term
  * split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi of FP32 operands into TF32
- * parts: FP32 accuracy (|error| <~ 1e-6 max|Z|), FP64 output.  Arguments as
- * for mlmc_kl_field (n <= 65535 * 256).  MLMC_PREC_MIXED pipelines use it on
- * the levels whose inner solves run in FP32; the others use mlmc_kl_field.
- * A tile whose bounded wait for the tensor cores runs out leaves its outputs
- * unwritten and is reported by the next mlmc_run / mlmc_run_more as
- * MLMC_ERR_TIMEOUT. */
+ * parts: FP32 accuracy (|error| <~ 1e-6 max|Z|), FP64 output.  xi, n, Z as
+ * for mlmc_kl_field (n <= 65535 * 256); ws: device workspace of
+ * mlmc_kl_tc_workspace_bytes(ctx, n) bytes, 256-byte aligned (the split
+ * sample operand, written and read by the call).  MLMC_PREC_MIXED pipelines
+ * use it on the levels whose inner solves run in FP32; the others use
+ * mlmc_kl_field.  A tile whose bounded wait for the tensor cores runs out
+ * leaves its outputs unwritten and is reported by the next mlmc_run /
+ * mlmc_run_more as MLMC_ERR_TIMEOUT. */
+mlmc_status mlmc_kl_tc_workspace_bytes(const mlmc_ctx* ctx, int n, size_t* bytes);
 mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
-                             void* stream);
+                             void* ws, size_t ws_bytes, void* stream);
 
 /* Rows a3-a8 -- per-sample solve on grid level l: conductivity from Z, Q1
  * assembly, implicit Euler over all m_l steps with Newton (Sec. 3.3, 3.5),

@@ -89,7 +89,8 @@ def lib():
             "mlmc_workspace_bytes": ([vp, ip, ip, C.POINTER(sz)], ip),
             "mlmc_xi": ([vp, u64, ip, vp, ip, vp, vp], ip),
             "mlmc_kl_field": ([vp, ip, vp, ip, vp, vp], ip),
-            "mlmc_kl_field_tc": ([vp, ip, vp, ip, vp, vp], ip),
+            "mlmc_kl_tc_workspace_bytes": ([vp, ip, C.POINTER(sz)], ip),
+            "mlmc_kl_field_tc": ([vp, ip, vp, ip, vp, vp, sz, vp], ip),
             "mlmc_solve": ([vp, ip, vp, ip, vp, vp, vp, vp, sz, vp], ip),
             "mlmc_slab_residual": ([vp, ip, vp, vp, ip, vp, vp, vp], ip),
             "mlmc_activation": ([vp, ip, vp, ip, vp, vp], ip),
@@ -130,7 +131,8 @@ def lib():
 def exported_symbols():
     """Names of the C-ABI functions this binding declares."""
     return ["mlmc_create", "mlmc_destroy", "mlmc_last_error", "mlmc_level_info",
-            "mlmc_workspace_bytes", "mlmc_xi", "mlmc_kl_field", "mlmc_kl_field_tc", "mlmc_solve",
+            "mlmc_workspace_bytes", "mlmc_xi", "mlmc_kl_field", "mlmc_kl_tc_workspace_bytes",
+            "mlmc_kl_field_tc", "mlmc_solve",
             "mlmc_slab_residual",
             "mlmc_activation", "mlmc_sample_level", "mlmc_accumulate", "mlmc_reset",
             "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_run_more",
@@ -299,8 +301,12 @@ class Context:
         import torch
         _, cells, _ = self.level_info(level)
         xi = xi.contiguous()
-        out = torch.empty((xi.shape[0], cells), dtype=torch.float64, device="cuda")
-        self._check(lib().mlmc_kl_field_tc(self.h, level, _p(xi), xi.shape[0], _p(out),
+        n = xi.shape[0]
+        out = torch.empty((n, cells), dtype=torch.float64, device="cuda")
+        b = C.c_size_t()
+        self._check(lib().mlmc_kl_tc_workspace_bytes(self.h, n, C.byref(b)))
+        ws = self.workspace(max(b.value, 256), key="kl_tc")
+        self._check(lib().mlmc_kl_field_tc(self.h, level, _p(xi), n, _p(out), _p(ws), ws.numel(),
                                            _stream(stream)))
         return out
 

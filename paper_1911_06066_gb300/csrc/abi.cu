@@ -95,6 +95,7 @@ PairWs mlmc::pair_ws(const mlmc_ctx* c, int level, int n) {
   const LevelDesc& lf = c->lv[level];
   size_t off = 0;
   w.xi = off; off += align256((size_t)n * c->M * 8);
+  w.kl = off; off += c->cfg.precision == MLMC_PREC_MIXED ? kl_tc_workspace_bytes(c->M, n) : 0;
   w.Zf = off; off += align256((size_t)n * lf.cells * 8);
   w.Zc = off; off += level > 0 ? align256((size_t)n * c->lv[level - 1].cells * 8) : 0;
   w.tf = off; off += align256((size_t)n * lf.nodes * 8);
@@ -188,6 +189,7 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   sp.lin_max = c.lin_max;
   sp.ls_full_step = 1e-6;
   sp.step_max = __builtin_huge_val();   // set per level in solve_into
+  sp.cg_scale = 0;                      // likewise
 
   // KL mode table and per-level 1D mode values at the cell centroids
   ctx->M = c.kl_modes;
@@ -215,6 +217,9 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
       kl_phi_table_host(c.L[d], c.kl_ell, n1d[d], ctx->lv[l].n[d], tab);
       if ((e = cudaMalloc(&ctx->d_phi[l][d], sizeof(double) * tab.size())) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
       if ((e = cudaMemcpy(ctx->d_phi[l][d], tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
+      std::vector<float> tab32(tab.begin(), tab.end());
+      if ((e = cudaMalloc(&ctx->d_phi32[l][d], sizeof(float) * tab32.size())) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+      if ((e = cudaMemcpy(ctx->d_phi32[l][d], tab32.data(), sizeof(float) * tab32.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
     }
   int64_t n0 = ctx->lv[0].nodes;
   int L = c.n_levels;
@@ -240,7 +245,10 @@ extern "C" void mlmc_destroy(mlmc_ctx* ctx) {
   cudaFree(ctx->d_sqrt_lam);
   cudaFree(ctx->d_idx);
   for (int l = 0; l < MLMC_MAX_LEVELS; ++l)
-    for (int d = 0; d < 3; ++d) cudaFree(ctx->d_phi[l][d]);
+    for (int d = 0; d < 3; ++d) {
+      cudaFree(ctx->d_phi[l][d]);
+      cudaFree(ctx->d_phi32[l][d]);
+    }
   cudaFree(ctx->d_acc);
   cudaFree(ctx->d_N);
   cudaFree(ctx->d_est);
@@ -320,16 +328,25 @@ extern "C" mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi,
   return MLMC_OK;
 }
 
+extern "C" mlmc_status mlmc_kl_tc_workspace_bytes(const mlmc_ctx* ctx, int n, size_t* bytes) {
+  if (!ctx || !bytes || n < 0) return MLMC_ERR_ARG;
+  *bytes = kl_tc_workspace_bytes(ctx->M, n);
+  return MLMC_OK;
+}
+
 extern "C" mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* xi, int n,
-                                        double* Z, void* stream) {
+                                        double* Z, void* ws, size_t ws_bytes, void* stream) {
   if (!ctx) return MLMC_ERR_ARG;
   if (bad_level(ctx, level)) return MLMC_ERR_ARG;
   if (n < 0 || n > 65535 * 256 || (n > 0 && (!xi || !Z)))
     return fail(ctx, MLMC_ERR_ARG, "mlmc_kl_field_tc: bad arguments");
+  if (n == 0) return MLMC_OK;
+  if (!check_ws(ctx, ws, ws_bytes, kl_tc_workspace_bytes(ctx->M, n))) return MLMC_ERR_WORKSPACE;
   CK(ctx, launch_kl_field_tc(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_idx,
-                             ctx->d_phi[level][0], ctx->d_phi[level][1], ctx->d_phi[level][2], xi,
-                             n, Z, ctx->d_cnt + 6, (cudaStream_t)stream));
-  ctx->launches += 1;
+                             ctx->d_phi32[level][0], ctx->d_phi32[level][1],
+                             ctx->d_phi32[level][2], xi, n, Z, ws, ctx->d_cnt + 6,
+                             (cudaStream_t)stream));
+  ctx->launches += 2;
   return MLMC_OK;
 }
 
@@ -337,9 +354,11 @@ extern "C" mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* 
 // whose inner solves run in FP32 (MLMC_PREC_MIXED and c dt max r' <=
 // mixed_cdr_max), in FP64 elsewhere -- where the root selection is sensitive
 // to perturbations of the field, the field stays exact to FP64 rounding.
+// kws: kl_tc_workspace_bytes(M, n) bytes of the pair workspace.
 static mlmc_status kl_into(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
-                           cudaStream_t st) {
-  if (level_mixed(ctx->cfg, ctx->lv[level])) return mlmc_kl_field_tc(ctx, level, xi, n, Z, st);
+                           char* kws, cudaStream_t st) {
+  if (level_mixed(ctx->cfg, ctx->lv[level]))
+    return mlmc_kl_field_tc(ctx, level, xi, n, Z, kws, kl_tc_workspace_bytes(ctx->M, n), st);
   return mlmc_kl_field(ctx, level, xi, n, Z, st);
 }
 
@@ -400,6 +419,7 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
   SolverParams sp = ctx->sp;
   sp.lin_rtol = mixed ? fmax(ctx->cfg.lin_rtol, 1e-5) : ctx->cfg.lin_rtol;
   sp.step_max = step_limit(ctx->cfg.c, ctx->cfg.a, lv.dt);
+  sp.cg_scale = mixed && cg_needs_scaling(lv) ? 1 : 0;
   if (use_cluster) {
     ClusterGlobal g;
     g.u = (double*)(ws + w.ubuf);
@@ -567,12 +587,12 @@ mlmc_status mlmc::sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, con
   CK(ctx, launch_xi(seed, seeds, level, ids, n, ctx->M, xi, st_f));
   ctx->launches += 1;
   mlmc_status r;
-  if ((r = kl_into(ctx, level, xi, n, Zf, st_f)) != MLMC_OK) return r;
+  if ((r = kl_into(ctx, level, xi, n, Zf, ws + w.kl, st_f)) != MLMC_OK) return r;
   double* tc = nullptr;
   if (level > 0) {
     double* Zc = (double*)(ws + w.Zc);
     tc = t_coarse ? t_coarse : (double*)(ws + w.tc);
-    if ((r = kl_into(ctx, level - 1, xi, n, Zc, st_f)) != MLMC_OK) return r;
+    if ((r = kl_into(ctx, level - 1, xi, n, Zc, ws + w.kl, st_f)) != MLMC_OK) return r;
     if ((r = order_after(ctx, st_f, st_c)) != MLMC_OK) return r;
     if ((r = solve_into(ctx, level - 1, Zc, n, tc, nullptr, inf + n, ws + w.solve_c, st_c, stim)) !=
         MLMC_OK)

@@ -16,6 +16,7 @@ struct mlmc_ctx {
   double* d_sqrt_lam = nullptr;
   int* d_idx = nullptr;
   double* d_phi[MLMC_MAX_LEVELS][3] = {};
+  float* d_phi32[MLMC_MAX_LEVELS][3] = {};   // FP32 copies (tensor-core KL synthesis)
   double* d_acc = nullptr;        // [3][levels][nodes0]: mean, M2, mean of Y2
   int64_t* d_N = nullptr;         // [levels]
   double* d_est = nullptr;        // estimate output
@@ -53,7 +54,7 @@ mlmc_status cuda_fail(mlmc_ctx* ctx, cudaError_t e, const char* where);
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct PairWs {
-  size_t xi, Zf, Zc, tf, tc, info, solve_f, solve_c, total;
+  size_t xi, kl, Zf, Zc, tf, tc, info, solve_f, solve_c, total;
 };
 // Workspace of n level-l pairs (xi, both fields, both activation maps, info
 // and the two solves' scratch), 256-byte aligned offsets.

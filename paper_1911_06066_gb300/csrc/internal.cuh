@@ -42,7 +42,13 @@ struct SolverParams {
   int lin_max;
   double ls_full_step;   // max|d| below which the full Newton step is taken
   double step_max;       // largest nodal move per Newton iteration (inf: none)
+  int cg_scale;          // FP32 CG: solve for a power-of-two scaled right-hand side
 };
+
+// FP32 inner solves on grids whose lumped mass per time step is this small
+// (the fine 3D levels) scale the CG's right-hand side by a power of two: their
+// late Newton residuals otherwise push the CG's r.z below FP32's normal range.
+inline bool cg_needs_scaling(const LevelDesc& lv) { return lv.vol / lv.dt < 1e-4; }
 
 // Geometric multigrid hierarchy of one grid level (the CG preconditioner of
 // the global-memory cluster layout).  Level 0 is the level's own grid; level
@@ -115,10 +121,13 @@ cudaError_t launch_kl_field(const LevelDesc& lv, int M, const double* sqrt_lam, 
 // Mixed-precision KL synthesis on the tensor cores (kl_tc.cu): three-term
 // split-TF32 products, FP32 accumulation in tensor memory, FP64 output.  err
 // (device) counts CTAs whose bounded wait for the tensor cores ran out.
+// ws: kl_tc_workspace_bytes(M, n) bytes (the prepared B operand), 256-byte
+// aligned; phi_*: the 1D mode tables in FP32.
+size_t kl_tc_workspace_bytes(int M, int n);
 cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
-                               const double* phi_x, const double* phi_y, const double* phi_z,
-                               const double* xi, int n, double* Z, unsigned long long* err,
-                               cudaStream_t st);
+                               const float* phi_x, const float* phi_y, const float* phi_z,
+                               const double* xi, int n, double* Z, void* ws,
+                               unsigned long long* err, cudaStream_t st);
 cudaError_t preload_kl_tc();
 cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,
                             double* coef64, float* coef32, cudaStream_t st);

@@ -118,6 +118,7 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int level, con
   sp.lin_max = c.lin_max;
   sp.ls_full_step = 1e-6;
   sp.step_max = step_limit(c.c, c.a, lv.dt);
+  sp.cg_scale = 0;   // the block kernel does not scale
 
   // scratch layout of mlmc_solve's workspace, carved from the static array
   size_t N = (size_t)nodes, NO = (size_t)n_offsets(c.dim), kr = mixed ? 4 : 8;

@@ -364,13 +364,17 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     int it;
     for (it = 1; it <= sp.newton_max; ++it) {
       // residual, Hessian diagonal and the CG start r = -F, z = P^-1 r, p = z, d = 0
-      // FP32 CG: the right-hand side is scaled by a power of two sigma with
-      // max|F| sigma in [1, 2), and d by 1/sigma after the solve.  Both are
-      // exact, so this changes nothing except that the CG's products stay in
-      // FP32's normal range: on fine 3D grids (lumped mass ~ h^3) the late
-      // Newton residuals are ~1e-18 and the CG's r.z fell below 1e-38.
-      constexpr bool SCALE = sizeof(KR) == 4;
-      double fmax_loc = 0.0;
+      // FP32 CG on grids with a tiny lumped mass per time step (sp.cg_scale,
+      // the fine 3D levels): the right-hand side is scaled by a power of two
+      // sigma with ||F||_2 sigma in [1, 2), and d by 1/sigma after the solve.
+      // Both are exact, so this changes nothing except that the CG's products
+      // stay in FP32's normal range: on the 256 x 256 x 64 level (lumped mass
+      // ~ h^3) the late Newton residuals are ~1e-18 and the CG's r.z fell below
+      // 1e-38.  One FP64 reduction gives sum F^2 (for sigma) and sum F^2 /
+      // |H_ii| (the CG's first r.z, = sigma^-2 r.z), so the scaling costs one
+      // local pass and a barrier per Newton iteration.
+      const bool SCALE = sizeof(KR) == 4 && sp.cg_scale != 0;
+      double f2_loc = 0.0, f2p_loc = 0.0;
       KR rz_loc = 0;
       for (int a = tid; a < b.nb; a += NT) {
         const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
@@ -381,7 +385,6 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c)), uA = u[a];
         const double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
         F[a] = f;
-        fmax_loc = fmax(fmax_loc, fabs(f));
         // Hessian diagonal and Jacobi inverse in the CG's precision (the CG is
         // the only user); no FP64 division on the per-node path
         const KR uK = (KR)uA, mK = (KR)mA;
@@ -392,7 +395,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         const KR pvv = MG ? (KR)1 / (fabs(hmA) + mgb[mg.l[0].ks + A])   // l1-Jacobi (V-cycle smoother)
                           : (KR)1 / fabs(hmA + (KR)c64[(int64_t)CTR * N + A]);
         pinv[a] = pvv;
-        if (!SCALE) {
+        if (SCALE) {
+          f2_loc += f * f;
+          f2p_loc += f * f * (double)pvv;
+        } else {
           const KR rv = (KR)(-f);
           r[a] = rv;
           if (!MG) {
@@ -402,20 +408,21 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           }
         }
       }
-      double sigma = 1.0;
+      double sigma = 1.0, rz_scaled = 0.0;
       if (SCALE) {
-        double v1[1] = {fmax_loc};
-        cluster_reduce<NT, double, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
-        if (bc[0] > 0.0) sigma = ldexp(1.0, -ilogb(bc[0]));
+        double v2[2] = {f2_loc, f2p_loc};
+        cluster_reduce<NT, double, 2>(v2, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+        if (bc[0] > 0.0) sigma = ldexp(1.0, -ilogb(sqrt(bc[0])));
+        rz_scaled = bc[1] * sigma * sigma;
         for (int a = tid; a < b.nb; a += NT) {
           const KR rv = (KR)(-F[a] * sigma);
           r[a] = rv;
           if (!MG) {
             const KR zv = pinv[a] * rv;
             z[a] = zv; p[a] = zv;
-            rz_loc += rv * zv;
           }
         }
+        if (!MG) cluster_barrier(cl, b.C);   // p is read across the cluster next
       }
       if (MG) {
         cluster_barrier(cl, b.C);
@@ -428,11 +435,11 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           rz_loc += r[a] * zv;
         }
       }
-      {
+      if (MG || !SCALE) {
         KR v1[1] = {rz_loc};
         cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
       }
-      double rz = bc[0];
+      double rz = MG || !SCALE ? bc[0] : rz_scaled;
       const double rz_stop = rtol2 * rz;
       int cgi = 0;
       bool truncated = false;
