@@ -247,17 +247,23 @@ def run_ours(args, w):
             torch.cuda.synchronize()
             return ev0.elapsed_time(ev1)
 
-        t_tuned = estimate_ms()
+        # greedy over the levels, from the automatic layouts: a level takes its
+        # tuned layout only if the whole estimate gets faster
         for l in range(w["levels"]):
             ctx.set_layout(l, 0)
-        t_auto = estimate_ms()
-        keep = t_tuned < t_auto
-        if keep:
-            for l in range(w["levels"]):
-                ctx.set_layout(l, layouts[l]["layout"])
-        layouts["whole_estimate_ms"] = {"per_level_tuned": round(t_tuned, 1),
-                                        "automatic": round(t_auto, 1),
-                                        "kept": "per_level_tuned" if keep else "automatic"}
+        t_best = estimate_ms()
+        trail = [{"layouts": [0] * w["levels"], "ms": round(t_best, 1)}]
+        for l in range(w["levels"]):
+            if layouts[l]["layout"] == 0:
+                continue
+            ctx.set_layout(l, layouts[l]["layout"])
+            t = estimate_ms()
+            trail.append({"layouts": [ctx.layout(k) for k in range(w["levels"])], "ms": round(t, 1)})
+            if t < t_best:
+                t_best = t
+            else:
+                ctx.set_layout(l, 0)
+        layouts["whole_estimate_ms"] = trail
 
     def barrier():
         if world > 1:
