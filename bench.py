@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the automatic solve layouts instead of the autotuner's choice")
+    ap.add_argument("--layouts", default=None, metavar="L0,L1,...",
+                    help="use these per-level layout codes (mlmc_set_layout) instead of tuning")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch each estimate's kernels directly instead of as one CUDA graph")
     ap.add_argument("--no-extras", action="store_true",
@@ -233,7 +235,12 @@ def run_ours(args, w):
     # choice is kept only if a whole estimate is faster with it than with the
     # automatic layouts (each timed on its second run).
     layouts = {}
-    if not args.no_tune:
+    if args.layouts:
+        codes = [int(x) for x in args.layouts.split(",")]
+        for l, c in enumerate(codes[:w["levels"]]):
+            ctx.set_layout(l, c)
+        layouts = {"given": codes}
+    elif not args.no_tune:
         for l in range(w["levels"]):
             best, ms = ctx.autotune(l, min(w["N"][l], batch), seed=seed + 1000)
             layouts[l] = {"layout": best, "ms": {str(k): round(v, 2) for k, v in ms.items()}}
