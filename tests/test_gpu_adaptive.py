@@ -136,6 +136,8 @@ def test_run_to_rmse_allocation_and_estimate(precision):
     est = O.mlmc_estimate(lvs, w["sigma2"], w["ell"], w["M"], 4, [int(n) for n in N], threads=8)
     tol = 1e-6 if precision == B.MLMC_PREC_FP64 else 1e-4
     np.testing.assert_allclose(res["mean"], est["mean"], atol=tol * w["T"])
+    # the mixed-precision MLMC mean is within 0.1 eps of the FP64 one
+    assert np.abs(res["mean"] - est["mean"]).max() <= 0.1 * eps
     np.testing.assert_allclose(V, est["V_l"], rtol=1e-4, atol=1e-8)
     assert math.isclose(res["bias"], est["bias"], rel_tol=1e-4, abs_tol=1e-8)
     assert math.isclose(res["rmse"], math.sqrt(float(np.sum(V / N)) + res["bias"] ** 2), rel_tol=1e-10)

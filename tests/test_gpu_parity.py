@@ -361,3 +361,27 @@ def test_full_size_level2_pair_sampled():
     assert all(i["status"] == 0 for i in B.info_dicts(info))
     d = np.abs(y[0].cpu().numpy() - yo)
     assert np.sort(d)[-3] <= T_TOL * w["T"]          # allow <= 2 threshold-ambiguous nodes
+
+
+@pytest.mark.parametrize("precision", [B.MLMC_PREC_MIXED], ids=["mixed"])
+def test_full_size_3d_level2_certified_by_the_slab_residual(precision):
+    """The 3D slab's 128 x 128 x 32 level at full size (549,153 nodes, 128
+    steps) in the benchmark's precision and automatic layout (global-memory
+    clusters): too large for the oracle, so the solve is checked by what holds
+    at any size -- the all-at-once residual of Eq. mono_disc over every slice
+    vanishes to the Newton tolerance, the activation map recomputed from the
+    stored slab equals the one extracted on the fly, and the front has moved."""
+    w = W.SLAB3D_4LVL
+    level = 2
+    ctx = ctx_for(w, precision)
+    Z = ctx.kl_field(level, ctx.xi(0, level, torch.tensor([5])))
+    t, slab, info = ctx.solve(level, Z, slab=True)
+    torch.cuda.synchronize()
+    assert B.info_dicts(info)[0]["status"] == 0, B.info_dicts(info)
+    _, rmax = ctx.slab_residual(level, Z, slab, full=False)
+    # |F| / M_i <= (1/dt + |K_ii| / M_i) max|d| ~ 2e-10 for max|d| <= 1e-12
+    assert rmax.item() <= 1e-8, rmax.item()
+    t2 = ctx.activation(level, slab)
+    assert torch.max(torch.abs(t - t2)).item() <= 1e-12 * w["T"]
+    tn = t[0].cpu().numpy()
+    assert (tn < w["T"]).sum() > 1000 and (tn == 0.0).sum() > 0
