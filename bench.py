@@ -246,30 +246,56 @@ def run_ours(args, w):
             layouts[l] = {"layout": best, "ms": {str(k): round(v, 2) for k, v in ms.items()}}
 
         def estimate_ms():
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            # as the timed steps: one untimed run, then the mean of two runs,
+            # each after an L2 flush
+            ctx.run(w["N"], seed=seed + 2000, batch=batch)
+            tot = 0.0
             for _ in range(2):
+                flush.zero_()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 ev0.record(stream)
                 ctx.run(w["N"], seed=seed + 2000, batch=batch)
                 ev1.record(stream)
-            torch.cuda.synchronize()
-            return ev0.elapsed_time(ev1)
+                torch.cuda.synchronize()
+                tot += ev0.elapsed_time(ev1)
+            return tot / 2
 
-        # greedy over the levels, from the automatic layouts: a level takes its
-        # tuned layout only if the whole estimate gets faster
-        for l in range(w["levels"]):
-            ctx.set_layout(l, 0)
-        t_best = estimate_ms()
-        trail = [{"layouts": [0] * w["levels"], "ms": round(t_best, 1)}]
-        for l in range(w["levels"]):
-            if layouts[l]["layout"] == 0:
-                continue
-            ctx.set_layout(l, layouts[l]["layout"])
+        # every combination of (automatic, tuned) per level for up to three
+        # levels, else greedy over the levels from the automatic layouts
+        import itertools
+        L = w["levels"]
+        tuned = [layouts[l]["layout"] for l in range(L)]
+        trail = []
+
+        def trial(choice):
+            for l in range(L):
+                ctx.set_layout(l, tuned[l] if choice[l] else 0)
             t = estimate_ms()
-            trail.append({"layouts": [ctx.layout(k) for k in range(w["levels"])], "ms": round(t, 1)})
-            if t < t_best:
-                t_best = t
-            else:
-                ctx.set_layout(l, 0)
+            trail.append({"layouts": [ctx.layout(k) for k in range(L)], "ms": round(t, 1)})
+            return t
+
+        if L <= 3:
+            combos = [c for c in itertools.product((0, 1), repeat=L)
+                      if all(tuned[l] != 0 or not c[l] for l in range(L))]
+            times = {c: trial(c) for c in combos}
+            best = min(times, key=times.get)
+            # the automatic layouts unless another combination is >= 1 % faster
+            auto = tuple([0] * L)
+            if times[best] > 0.99 * times[auto]:
+                best = auto
+        else:
+            best = [0] * L
+            t_best = trial(best)
+            for l in range(L):
+                if tuned[l] == 0:
+                    continue
+                cand = list(best)
+                cand[l] = 1
+                t = trial(cand)
+                if t < 0.99 * t_best:
+                    best, t_best = cand, t
+        for l in range(L):
+            ctx.set_layout(l, tuned[l] if best[l] else 0)
         layouts["whole_estimate_ms"] = trail
 
     def barrier():
