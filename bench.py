@@ -42,6 +42,12 @@ FP64_PEAK_TFLOPS = 1.01
 # iteration (residual: stencil 18, mass and reaction terms 12; update 2).
 FLOP_CG_NODE = 31
 FLOP_NEWTON_NODE = 32
+# DRAM bytes (read + write) per solve launch of one estimate of the 3-level 2D
+# workload, mean over its 5 launches: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the timed estimate (automatic layouts; 184 MB per
+# estimate).  The sweep keeps each sample's state on chip, so this is far
+# below any streamed-stencil traffic.
+TRAFFIC_2D_BYTES_PER_SOLVE_LAUNCH = 36.85e6
 # Algorithmic HBM bytes per node of the 3D global-memory sweep (couplings are
 # streamed from HBM every pass; 27 per node): an FP32 CG iteration reads 27
 # FP32 couplings and touches 14 FP32 vector words (164 B); an FP64 one 27 FP64
@@ -377,7 +383,10 @@ def run_ours(args, w):
         "roofline": roofline_3d(cg64_ni, cg_ni, nw_ni, solve_ms, dev_ms,
                                                       nsolve / args.steps) if w["dim"] == 3 else
                     {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     # measured with the automatic layouts only
+                     "traffic": TRAFFIC_2D_BYTES_PER_SOLVE_LAUNCH if all(
+                         ctx.layout(l) == 0 for l in range(w["levels"])) else None,
                      "kernel": "solve_cluster_kernel (per-sample Newton-CG sweep), FP64 pipe",
                      "peak_source": "FP64 FMA-chain probe on GB300 (measured)",
                      "aggregate_tflops": aggregate, "aggregate_frac": aggregate / FP64_PEAK_TFLOPS,
