@@ -193,7 +193,15 @@ def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, 
                 lin_max=5000, levels=None, solver=MLMC_SOLVER_AUTO, mixed_cdr_max=0.0,
                 cluster_size=0, precond=MLMC_PRECOND_JACOBI, mg_nu=0, mg_coarse_sweeps=0,
                 use_graph=False):
-    """mlmc_config from a workload dictionary (see workloads.py)."""
+    """mlmc_config from a workload dictionary (see workloads.py).
+
+    precision: MLMC_PREC_FP64 or MLMC_PREC_MIXED (FP32 inner solves and the
+    tensor-core KL field on levels with c dt max r' <= mixed_cdr_max).
+    solver / cluster_size: kernel layout of the per-sample sweep.
+    precond: MLMC_PRECOND_JACOBI or MLMC_PRECOND_GMG (geometric multigrid on
+    levels whose step Hessians are positive definite; mg_nu / mg_coarse_sweeps
+    its smoothing counts, 0 = defaults).  use_graph: launch each run's whole
+    schedule as one CUDA graph (needs a non-default stream)."""
     c = mlmc_config()
     c.dim = w["dim"]
     c.n_levels = levels if levels is not None else w["levels"]
