@@ -127,3 +127,29 @@ def test_stimulus_nodes():
     # nodes (i, j) with i^2 + j^2 < (0.1 * 32)^2 = 10.24
     expect = np.array([[1.0 if i * i + j * j <= 10 else 0.0 for i in range(33)] for j in range(33)])
     assert np.array_equal(u0, expect) and u0.sum() == 13
+
+
+@pytest.mark.parametrize("dim,ns", [(2, (4, 8, 16, 32)), (3, (4, 8, 16))])
+def test_spatial_convergence_rate_against_the_heat_equation(dim, ns):
+    """Manufactured solution: with c = 0 and D = I, u = exp(-dim pi^2 t)
+    prod_d cos(pi x_d) solves u_t = div grad u with Neumann data on the unit
+    box.  Implicit Euler with the exact spatial operator maps the mode by
+    1 / (1 + dt dim pi^2) per step, so comparing the oracle's slab with that
+    factor isolates the spatial error, which for Q1 with lumped mass must
+    fall as h^2 (ratio 4 per halving)."""
+    m, T = 10, 0.05
+    dt = T / m
+    errs = []
+    for n in ns:
+        lv = level(dim, (n,) * dim, m=m, T=T, c=0.0)
+        x = np.arange(n + 1) / n
+        v1 = np.cos(math.pi * x)
+        u0 = v1
+        for _ in range(dim - 1):
+            u0 = np.kron(v1, u0)
+        slab, _, _ = O.solve_sample(lv, np.zeros(lv.cells), u0=u0)
+        exact = u0 / (1 + dt * dim * math.pi ** 2) ** m
+        errs.append(np.abs(slab[m] - exact).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.8 < r < 4.2 for r in ratios[1:]), (errs, ratios)
+    assert 3.5 < ratios[0] < 4.5, (errs, ratios)
