@@ -2,7 +2,7 @@
  * mlmc.h -- C ABI of the GB300 space-time multilevel Monte Carlo library for
  * the stochastic monodomain equation (arXiv:1911.06066).
  *
- * Problem (Sec. 2.1, Eq. monodomain and Eq. ionic_term; Sec. 2.2,
+ * Problem (Sec. 2.1, Eq. monodomain and Eq. ionic_term; Sec. 3.1.1,
  * Eq. KL-expansion), in the variant this library implements:
  *     u_t = div(D grad u) + c u (1-u) (u-a)   on a box, Neumann boundary,
  *     D   = s_t I + (s_l - s_t) f f^T,  s_l = s_l0 exp(Z),  f = (cos th, sin th, 0),
@@ -10,9 +10,15 @@
  *     u(x,0) = 1 inside the ball |x - x_c| < stim_r, else 0,
  * discretised by Q1 elements with lumped mass and implicit Euler (the block
  * lower-bidiagonal space-time system of Sec. 3.2, Eq. system_C, with the
- * reaction of Sec. 3.3, Eq. mono_disc), solved by Newton.  The quantity of
+ * reaction of Sec. 3.3, Eq. mono_disc), solved step by step.  Where a step
+ * has several roots (c dt max r' > 1, max r' = c((1+a)^2/3 - a)) the root is
+ * the end point of the gradient flow M v' = -F_k(v) of the step's energy
+ * started at u_{k-1} -- the local minimum in whose basin u_{k-1} lies -- which
+ * the solver reaches by a gradient-flow continuation (linearly implicit
+ * pseudo-steps, then Newton); elsewhere the root is unique and Newton with a
+ * line search finds it.  The quantity of
  * interest is the activation time (first t with u >= 1/2, linear in t).  Its
- * mean and variance are estimated by MC / MLMC (Sec. 2.2, Eq. MC-estimator,
+ * mean and variance are estimated by MC / MLMC (Sec. 3.1.2, Eq. MC-estimator,
  * Eq. MLMC-estimator).
  *
  * Conventions for every call:
@@ -73,8 +79,10 @@ typedef struct {
   double kl_ell;
   int kl_modes;
   int precision;         /* mlmc_precision                                           */
-  double newton_tol;     /* stop when max |Newton correction| <= newton_tol          */
-  int newton_max;        /* Newton iterations per time step                          */
+  double newton_tol;     /* stop when an accepted correction moves no node by more
+                            than newton_tol                                          */
+  int newton_max;        /* nonlinear iterations (Newton or pseudo-steps, accepted or
+                            retried) per time step                                  */
   double lin_rtol;       /* CG relative tolerance (FP64 inner solves)                */
   int lin_max;           /* CG iterations per Newton step                            */
   int solver;            /* mlmc_solver: kernel layout of the per-sample sweep        */
@@ -126,10 +134,11 @@ typedef enum {
 typedef struct {
   int32_t status;        /* MLMC_OK or MLMC_ERR_NOT_CONVERGED                        */
   int32_t failed_step;   /* first step that did not converge (0 if none)             */
-  int32_t newton_iters;  /* summed over the time steps                               */
+  int32_t newton_iters;  /* nonlinear iterations summed over the time steps          */
   int32_t cg_iters;      /* summed over all Newton steps                             */
   int32_t truncations;   /* CG runs stopped at negative curvature                    */
-  int32_t halvings;      /* line-search step halvings                                */
+  int32_t halvings;      /* line-search step halvings, or retried pseudo-steps of the
+                            gradient-flow continuation                              */
   int32_t max_newton;    /* largest Newton count of one step                         */
   int32_t pad;
 } mlmc_sample_info;
@@ -137,7 +146,7 @@ typedef struct {
 typedef struct mlmc_ctx mlmc_ctx;
 
 /* Create a context for one configuration on the current CUDA device.
- * Builds the KL mode table (Sec. 2.2, Eq. KL-expansion-deterministic) on the
+ * Builds the KL mode table (Sec. 3.1.1, Eq. KL-expansion-deterministic) on the
  * host and copies it and the level descriptors to the device (small, owned by
  * the context).  *out is NULL on failure. */
 mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out);
@@ -154,7 +163,7 @@ mlmc_status mlmc_level_info(const mlmc_ctx* ctx, int level, int64_t* nodes, int6
  * samples of level l (256-byte aligned pointer required). */
 mlmc_status mlmc_workspace_bytes(const mlmc_ctx* ctx, int level, int n, size_t* bytes);
 
-/* Row a1 -- xi for n samples (Sec. 2.2: the psi_k / y_k of the KL expansion,
+/* Row a1 -- xi for n samples (Sec. 3.1.1: the psi_k / y_k of the KL expansion,
  * here standard normal): Philox4x32-10 (Salmon et al., SC'11) with
  *   counter = (mode pair j, lo32(id), hi32(id), level), key = (lo32(seed), hi32(seed)),
  * and Box-Muller with correctly rounded operations only, so that the values
@@ -163,7 +172,7 @@ mlmc_status mlmc_xi(mlmc_ctx* ctx, uint64_t seed, int level, const uint64_t* ids
                     double* xi, void* stream);
 
 /* Row a2 -- truncated KL field on the cell centroids of grid level l
- * (Sec. 2.2, Eq. KL-expansion-deterministic):
+ * (Sec. 3.1.1, Eq. KL-expansion-deterministic):
  *   Z[s][cell] = sum_k sqrt(lam_k) phi_k(centroid) xi[s][k].
  * xi: device [n][kl_modes]; Z: device [n][cells_l]. */
 mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
@@ -214,7 +223,7 @@ mlmc_status mlmc_slab_residual(mlmc_ctx* ctx, int level, const double* Z, const 
 mlmc_status mlmc_activation(mlmc_ctx* ctx, int level, const double* slab, int n, double* t_act,
                             void* stream);
 
-/* Rows a1-a9 -- n level-l sample pairs (Sec. 2.2, Eq. MLMC-estimator): one xi
+/* Rows a1-a9 -- n level-l sample pairs (Sec. 3.1.2, Eq. MLMC-estimator): one xi
  * per pair (counter level = l), the fine (l) and coarse (l-1) problems solved
  * with that xi, activation maps injected onto the level-0 vertices and
  *   y[s]  = t_l - t_{l-1},   y2[s] = t_l^2 - t_{l-1}^2     (t_{-1} = 0).
@@ -430,17 +439,26 @@ void mlmc_server_destroy(mlmc_server* s);
  * info device [n] or NULL, plus the configuration itself (no context needed).
  *
  * Scratch: one file-scope device array of MLMC_NOALLOC_SCRATCH_BYTES bytes,
- * reserved on every device that loads the library and held until the process
- * exits.  The call allocates nothing (no cudaMalloc/cudaFree, no allocating
- * library routine).  Requests whose scratch would exceed the array are
- * rejected with MLMC_ERR_WORKSPACE and a message naming both sizes (read it
- * with mlmc_last_error(NULL)); other failures set the same message.
- * The first call on a device looks up the array's device address (once per
- * device, under a lock); make that first call before any stream capture.
+ * held by every device that uses it until the process exits.  The call
+ * allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ * Requests whose scratch would exceed the array are rejected with
+ * MLMC_ERR_WORKSPACE and a message naming both sizes (read it with
+ * mlmc_last_error(NULL)); other failures set the same message.
+ * Set-up: the first call on a device (with that device current) looks up the
+ * array's device address and loads the modules of the kernels it launches,
+ * once per device, under a lock.  CUDA loads modules lazily by default, so it
+ * is this first call -- not the loading of the library -- that places the
+ * 16 MiB array and the kernels' code on the device.  Make that first call
+ * during the caller's own set-up (a call with n = 1 is enough), before any
+ * stream capture and while device memory can still be committed; later calls
+ * only enqueue the assembly and the sweep.
  * Every call on a device shares the one array and leaves its contents behind;
  * the solve writes every scratch word before reading it, so nothing needs
  * clearing, but calls whose work overlaps on the GPU (other streams, other
- * host threads) race on the scratch and must be serialised by the caller. */
+ * host threads) race on the scratch and must be serialised by the caller.
+ * The level geometry, precision rule and solver parameters are derived from
+ * cfg exactly as mlmc_create and mlmc_solve derive them; a level whose grid
+ * exceeds 2^31 nodes or 2^20 cells per axis is rejected with MLMC_ERR_ARG. */
 #define MLMC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int level, const double* Z, int n,
                                double* t_act, mlmc_sample_info* info, void* stream);

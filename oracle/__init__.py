@@ -7,7 +7,7 @@ import it; the product package never does, and the two share no code.
 
 The arithmetic lives in C (``rng.c``, ``kl.c``, ``fem.c``, ``solve.c``,
 ``mlmc.c``, built by ``build.py``); this module only marshals arguments and
-composes the estimators of Sec. 2.2 (Eq. MC-estimator, Eq. MLMC-estimator).
+composes the estimators of Sec. 3.1.2 (Eq. MC-estimator, Eq. MLMC-estimator).
 
 Functions without an independent pin are listed as "parity unpinned" in
 their docstrings (none at present).
@@ -63,7 +63,7 @@ class Level(C.Structure):
 
 
 def make_level(dim, n, m, L, T, c, a, s_t, s_l0, theta0, theta1=None, stim_r=0.1,
-               stim_c=(0.0, 0.0, 0.0), newton_tol=1e-12, newton_max=500,
+               stim_c=(0.0, 0.0, 0.0), newton_tol=1e-12, newton_max=5000,
                lin_rtol=1e-12, lin_max=5000):
     lv = Level()
     lv.dim = dim
@@ -103,6 +103,8 @@ def _declare(l):
     l.or_step_residual.argtypes = [lp, _dp, _dp, _dp, _dp, _dp]
     l.or_newton_cg.argtypes = [C.c_int, _dp, _dp, lp, _dp, _dp, _dp, C.POINTER(C.c_int)]
     l.or_step_solve.argtypes = [lp, _dp, _dp, _dp, _dp, _ip]
+    l.or_step_gradient_flow.argtypes = [lp, _dp, _dp, _dp, C.c_void_p, _dp, C.c_double, C.c_double,
+                                        C.c_int, _ip]
     l.or_solve_sample.argtypes = [lp, _dp, C.c_void_p, _dp, _dp, _ip]
     l.or_slab_residual.argtypes = [lp, _dp, _dp, _dp, _dp]
     l.or_activation.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
@@ -221,6 +223,27 @@ def step_solve(lv, mass, kst, u_prev):
     if rc < 0:
         raise RuntimeError("oracle step did not converge")
     return u, dict(zip(("newton", "cg", "truncations", "halvings"), st.tolist()))
+
+
+def step_gradient_flow(lv, mass, kst, u_prev, tau=None, ftol=1e-12, max_pseudo=1000000, v0=None):
+    """Solver-independent root of one implicit-Euler step: the end point of the
+    gradient flow M v' = -F(v) of the step energy started at u_prev (the local
+    minimum in whose basin u_prev lies; started at v0 instead when given), by
+    strictly convex implicit-Euler
+    pseudo-steps of length tau (default 1 / (2 (max r' - 1/dt)), which keeps every
+    pseudo-step strictly convex).  Returns (u, stats{pseudo, newton, cg})."""
+    if tau is None:
+        s = lv.c * ((1 + lv.a) ** 2 / 3 - lv.a) - lv.m / lv.T
+        tau = 0.5 / s if s > 0 else 1.0
+    u = np.zeros(lv.nodes)
+    st = np.zeros(3, np.int32)
+    v0c = None if v0 is None else np.ascontiguousarray(v0, np.float64)
+    rc = lib().or_step_gradient_flow(C.byref(lv), mass, kst, np.ascontiguousarray(u_prev, np.float64),
+                                     None if v0c is None else v0c.ctypes.data, u, float(tau),
+                                     float(ftol), int(max_pseudo), st)
+    if rc < 0:
+        raise RuntimeError("gradient flow did not reach the tolerance: %s" % st.tolist())
+    return u, dict(zip(("pseudo", "newton", "cg"), st.tolist()))
 
 
 def solve_sample(lv, Z, u0=None):

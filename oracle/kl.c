@@ -1,6 +1,6 @@
 /*
  * Oracle: truncated Karhunen-Loeve expansion of the log-conductivity
- * (Sec. 2.2, Eq. KL-expansion and KL-expansion-deterministic), in the variant
+ * (Sec. 3.1.1, Eq. KL-expansion and KL-expansion-deterministic), in the variant
  * with the separable exponential covariance
  *     k(x, y) = sigma2 * prod_d exp(-|x_d - y_d| / ell)
  * whose eigenpairs are products of 1D eigenpairs with a closed form.

@@ -1,5 +1,5 @@
 /*
- * Oracle: Monte Carlo and multilevel Monte Carlo estimators (Sec. 2.2,
+ * Oracle: Monte Carlo and multilevel Monte Carlo estimators (Sec. 3.1.2,
  * Eq. MC-estimator and Eq. MLMC-estimator, with u_{-1} = 0) on the activation
  * map, and the transfer of nodal fields between nested grids (Sec. 3.4; for
  * vertex-nested grids and a nodal quantity the transfer to the coarsest grid

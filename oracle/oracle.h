@@ -22,7 +22,7 @@ void or_sincos_2pi(double u, double* s, double* c); /* sin/cos of 2*pi*u      */
 /* xi[0..M) for (seed, level pair, sample id): standard normals, Box-Muller.   */
 void or_xi(uint64_t seed, int level, uint64_t sample_id, int M, double* xi);
 
-/* ---------- Karhunen-Loeve expansion (Sec. 2.2, Eq. KL-expansion) ---------- */
+/* ---------- Karhunen-Loeve expansion (Sec. 3.1.1, Eq. KL-expansion) ---------- */
 /* 1D eigenpairs of exp(-|x-y|/ell) on an interval of length len, modes 0..n-1
  * (decreasing eigenvalue).  omega[n], lam[n] (unit variance), nrm[n] = the
  * normalisation divisor; odd modes are sine modes. */
@@ -74,6 +74,15 @@ int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* l
  * stats = {newton its, cg its, truncations, halvings}.  Returns its or -1. */
 int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
                   const double* up, double* u, int* stats);
+/* Solver-independent root of one step: the end point of the mass-metric
+ * gradient flow M v' = -F(v) of the step energy from v(0) = up (or v0 when not
+ * NULL), integrated by
+ * strictly convex implicit-Euler pseudo-steps of length tau (requires
+ * tau (max r' - 1/dt) < 1) until max|F_i| / m_i <= ftol.  stats = {pseudo-steps,
+ * Newton iterations, CG iterations}.  Returns pseudo-steps, or -1. */
+int or_step_gradient_flow(const or_level* lv, const double* mass, const double* Kst,
+                          const double* up, const double* v0, double* u, double tau, double ftol,
+                          int max_pseudo, int* stats);
 /* Sequential implicit Euler + Newton for one sample.  u0 = NULL: the stimulus.
  * slab: [m+1][nodes] (slice 0 = u0), t_act: [nodes].
  * Returns total Newton iterations, or -(k) if step k failed to converge. */
@@ -86,7 +95,7 @@ void or_slab_residual(const or_level* lv, const double* mass, const double* Kst,
 void or_activation(int nodes, int m, double dt, double T, const double* slab,
                    double* t_act);
 
-/* ---------- MLMC (Sec. 2.2, Eqs. MC-estimator, MLMC-estimator) -------------- */
+/* ---------- MLMC (Sec. 3.1.2, Eqs. MC-estimator, MLMC-estimator) -------------- */
 /* Injection of a level-l nodal field onto the coarsest grid (level 0). */
 void or_inject(const or_level* fine, const or_level* l0, const double* f, double* out);
 typedef struct { long n; double* mean; double* m2; } or_welford;

@@ -1,5 +1,5 @@
 /*
- * Oracle: the random inputs xi of the KL expansion (Sec. 2.2, Eq. KL-expansion;
+ * Oracle: the random inputs xi of the KL expansion (Sec. 3.1.1, Eq. KL-expansion;
  * the workloads draw xi ~ N(0,1) from a counter-based Philox stream).
  * TEST INFRASTRUCTURE ONLY -- see oracle.h.
  *

@@ -11,32 +11,43 @@
  * H is symmetric, so F_k is the gradient of the step energy
  *   E(u) = (u-u_{k-1})^T M (u-u_{k-1}) / (2dt) + u^T K u / 2 - sum_i m_i R(u_i),
  *   R' = r,
- * and H is its Hessian.  When c dt max r' > 1 the step has several roots and
- * plain Newton from u_{k-1} cycles, so the root is defined (the paper is
- * silent) as the one reached from u_{k-1} by line-search Newton-CG on E
- * (Nocedal & Wright, Numerical Optimization, Alg. 7.1):
- *   - d from Jacobi-preconditioned CG (preconditioner |diag H|) on H d = -F,
- *     started at 0, stopped at relative preconditioned residual lin_rtol, and
- *     truncated at the first search direction p with p^T H p <= 0 (then the
- *     current iterate, or the preconditioned steepest-descent step if that
- *     happens in the first iteration);
- *   - stop when max|d| <= newton_tol (after applying d);
- *   - on strongly indefinite steps (c dt max r' > 2, max r' = c((1+a)^2/3 - a))
- *     the step starts at alpha = min(1, 0.1 / max|d|): no node moves by more
- *     than 0.1 per iteration, so the iterates follow the descent path instead
- *     of jumping between basins of attraction, which makes the selected root
- *     insensitive to rounding (with full steps, perturbations of one ulp in the
- *     couplings changed the root in 8 of 16 samples of a 3D level);
- *   - otherwise Armijo backtracking (halving, sigma = 1e-4, at most 40 halvings)
- *     on E(u + alpha d) - E(u) <= sigma alpha F^T d, with the energy change
- *     summed node by node in a cancellation-free form; when max|d| <= 1e-6 the
- *     full step is taken (the energy change is then below round-off).
- * Where H is positive definite this is plain Newton with full steps.
+ * and H is its Hessian.  When c dt max r' > 1 (max r' = c((1+a)^2/3 - a)) the
+ * step has several roots -- local minima of E -- and the paper is silent on
+ * which one the scheme means.  The root is defined as the end point of the
+ * gradient flow of E in the mass metric started at u_{k-1},
+ *   M v' = -F_k(v),  v(0) = u_{k-1},
+ * the minimum in whose basin of attraction u_{k-1} lies: a definition with no
+ * solver in it.  or_step_gradient_flow computes it plainly (fixed, strictly
+ * convex implicit-Euler pseudo-steps); or_step_solve reaches the same point
+ * faster by a gradient-flow continuation, and the tests pin the two together:
+ *   - linearly implicit pseudo-steps (M/t + H(u)) d = -F(u), u += d, by
+ *     Jacobi-preconditioned CG; t starts at 1/(2 max r'), doubles after every
+ *     accepted step and is capped at FLOW_CAP / max_i (r'(u_i) - 1/dt), which
+ *     keeps M/t + H positive definite (K is positive semidefinite).  Such a
+ *     step never reverses the sign of the flow's unstable component near a
+ *     saddle, so it does not jump between basins;
+ *   - a step that would move some node by more than FLOW_MOVE is retried with
+ *     a shorter t (counted as a halving);
+ *   - once an accepted step moves no node by more than FLOW_NEWTON the flow has
+ *     arrived near its minimum, and Newton steps (t = infinity) finish it as
+ *     long as their CG meets no non-positive curvature and they move no node
+ *     by more than 10 FLOW_NEWTON; otherwise the flow resumes;
+ *   - stop when an accepted step moves no node by more than newton_tol.
+ * Where c dt max r' <= 1, H is positive definite for every state, the root is
+ * unique, and plain Newton-CG with Armijo backtracking on E (sigma = 1e-4,
+ * halving, at most 40; full step when max|d| <= 1e-6) computes it.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 #include "oracle.h"
+
+/* Parameters of the gradient-flow continuation (see or_step_solve). */
+#define FLOW_CAP 0.5      /* pseudo-step t <= FLOW_CAP / max_i (r'(u_i) - 1/dt)   */
+#define FLOW_MOVE 0.3     /* largest nodal move of an accepted pseudo-step          */
+#define FLOW_TMIN 1e-9    /* pseudo-steps this short are accepted regardless        */
+#define FLOW_TMAX 1e20    /* upper bound of the growing pseudo-step                 */
+#define FLOW_NEWTON 1e-2  /* accepted move below which Newton steps finish the step  */
 
 static double rxn(double c, double a, double u) { return c * u * (1.0 - u) * (u - a); }
 static double rxn_d(double c, double a, double u) { return c * (-3.0 * u * u + 2.0 * (1.0 + a) * u - a); }
@@ -70,8 +81,13 @@ static double dot(int n, const double* a, const double* b) {
   return s;
 }
 
-int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* lv,
-                 const double* u_lin, const double* F, double* d, int* truncated) {
+/* Jacobi-preconditioned CG on (H + shift M) d = -F from d = 0, H the step
+ * Hessian at u_lin; truncated at the first search direction with p^T A p <= 0
+ * (then the current iterate, or the preconditioned steepest-descent step if
+ * that happens in the first iteration).  shift = 0: the Newton system. */
+static int shifted_cg(int n, const double* mass, const double* Kst, const or_level* lv,
+                      const double* u_lin, double shift, const double* F, double* d,
+                      int* truncated) {
   int no = lv->dim == 3 ? 27 : 9, ctr = lv->dim == 3 ? 13 : 4;
   double dt = lv->T / lv->m;
   double* pinv = malloc(sizeof(double) * n);
@@ -80,7 +96,8 @@ int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* l
   double* p = malloc(sizeof(double) * n);
   double* q = malloc(sizeof(double) * n);
   for (int i = 0; i < n; ++i) {
-    double dg = mass[i] / dt - mass[i] * rxn_d(lv->c, lv->a, u_lin[i]) + Kst[(size_t)i * no + ctr];
+    double dg = mass[i] * (shift + 1.0 / dt) - mass[i] * rxn_d(lv->c, lv->a, u_lin[i]) +
+                Kst[(size_t)i * no + ctr];
     pinv[i] = 1.0 / fabs(dg);
   }
   memset(d, 0, sizeof(double) * n);
@@ -92,6 +109,7 @@ int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* l
   if (r0 == 0.0) { ret = 0; goto done; }
   for (it = 1; it <= lv->lin_max; ++it) {
     hess_apply(lv, mass, Kst, u_lin, p, q);
+    for (int i = 0; i < n; ++i) q[i] += shift * mass[i] * p[i];
     double pq = dot(n, p, q);
     if (pq <= 0.0) {
       *truncated = 1;
@@ -110,6 +128,11 @@ int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* l
 done:
   free(pinv); free(r); free(z); free(p); free(q);
   return ret;
+}
+
+int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* lv,
+                 const double* u_lin, const double* F, double* d, int* truncated) {
+  return shifted_cg(n, mass, Kst, lv, u_lin, 0.0, F, d, truncated);
 }
 
 /* E(u + alpha d) - E(u), given Ku = K u and Kd = K d. */
@@ -138,29 +161,64 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
   int it, conv = 0, cg_total = 0, trunc_total = 0, halvings = 0;
   double dt = lv->T / lv->m;
   double rmax = lv->c * ((1.0 + lv->a) * (1.0 + lv->a) / 3.0 - lv->a);
-  double step_max = dt * rmax > 2.0 ? 0.1 : INFINITY;
+  const int flow = dt * rmax > 1.0;
+  double tau = 0.5 / rmax, sw = FLOW_NEWTON;
+  int newton_phase = 0;
   memcpy(u, up, sizeof(double) * n);
   for (it = 1; it <= lv->newton_max; ++it) {
     or_step_residual(lv, mass, Kst, u, up, F);
     int tr;
+    if (flow) {
+      /* linearly implicit pseudo-step of the gradient flow M v' = -F(v):
+         (M/t + H(u)) d = -F(u), t capped so that M/t + H stays positive
+         definite; once the flow has (nearly) arrived (an accepted move below
+         FLOW_NEWTON), Newton steps (t = infinity) finish the solve as long as
+         H is positive definite along their CG and they move no node by more
+         than 10 FLOW_NEWTON; a Newton step that fails either test is
+         discarded and the flow resumes with a tighter switch threshold */
+      double t = tau;
+      if (!newton_phase) {
+        double smax = -INFINITY;
+        for (int i = 0; i < n; ++i) {
+          double s = rxn_d(lv->c, lv->a, u[i]) - 1.0 / dt;
+          if (s > smax) smax = s;
+        }
+        if (smax > 0.0 && t > FLOW_CAP / smax) t = FLOW_CAP / smax;
+      }
+      int cg = shifted_cg(n, mass, Kst, lv, u, newton_phase ? 0.0 : 1.0 / t, F, d, &tr);
+      if (cg < 0) break;
+      cg_total += cg; trunc_total += tr;
+      double dmax = 0.0;
+      for (int i = 0; i < n; ++i) if (fabs(d[i]) > dmax) dmax = fabs(d[i]);
+      if (newton_phase) {
+        if (tr || dmax > 10.0 * sw) {
+          newton_phase = 0;
+          sw *= 0.1;
+          ++halvings;
+          continue;
+        }
+        for (int i = 0; i < n; ++i) u[i] += d[i];
+        if (dmax <= lv->newton_tol) { conv = 1; break; }
+        continue;
+      }
+      if (dmax > FLOW_MOVE && t > FLOW_TMIN) {
+        /* the step would move a node by more than FLOW_MOVE: retry shorter */
+        tau = t * 0.5 * FLOW_MOVE / dmax;
+        ++halvings;
+        continue;
+      }
+      for (int i = 0; i < n; ++i) u[i] += d[i];
+      if (dmax <= lv->newton_tol) { conv = 1; break; }
+      if (dmax <= sw) newton_phase = 1;
+      tau = fmin(2.0 * t, FLOW_TMAX);
+      continue;
+    }
     int cg = or_newton_cg(n, mass, Kst, lv, u, F, d, &tr);
     if (cg < 0) break;
     cg_total += cg; trunc_total += tr;
     double dmax = 0.0;
     for (int i = 0; i < n; ++i) if (fabs(d[i]) > dmax) dmax = fabs(d[i]);
     double alpha = 1.0;
-    if (dmax > step_max) {
-      /* max-norm trust region: clip every component to [-step_max, step_max];
-         if the clipped direction is not a descent direction of E, scale the
-         whole direction to max |d| = step_max instead */
-      double gdc = 0.0;
-      for (int i = 0; i < n; ++i) gdc += F[i] * fmin(fmax(d[i], -step_max), step_max);
-      if (gdc < 0.0) {
-        for (int i = 0; i < n; ++i) d[i] = fmin(fmax(d[i], -step_max), step_max);
-      } else {
-        alpha = step_max / dmax;
-      }
-    }
     if (dmax > lv->newton_tol && dmax > 1e-6) {
       double gd = dot(n, F, d);
       or_stiff_apply(lv, Kst, u, Ku);
@@ -178,6 +236,139 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
   if (stats) { stats[0] = it; stats[1] = cg_total; stats[2] = trunc_total; stats[3] = halvings; }
   free(F); free(d); free(Ku); free(Kd);
   return conv ? it : -1;
+}
+
+/*
+ * A solver-independent definition of the root of one step: the end point of
+ * the gradient flow of the step energy E (in the mass metric) started at
+ * u_{k-1},
+ *     M v'(s) = -F_k(v(s)),   v(0) = u_{k-1}  (or a given v0),
+ * i.e. the local minimum of E in whose basin of attraction u_{k-1} lies.  The
+ * flow is integrated by implicit-Euler pseudo-steps of fixed length tau,
+ *     v_{j+1} = argmin_w  E(w) + (w - v_j)^T M (w - v_j) / (2 tau),
+ * each of them a strictly convex problem when tau (max r' - 1/dt) < 1 (its
+ * Hessian M/tau + M/dt + K - M diag(r'(w)) is then positive definite, K being
+ * positive semidefinite), so every pseudo-step has exactly one solution, found
+ * by Newton's method with a CG solve to 1e-14 and backtracking on the convex
+ * objective.  No truncation, clipping, preconditioner or step-size choice
+ * enters the result.  Once max_i |F_k(v)_i| / m_i <= 1e-8 the flow is within
+ * ~1e-9 of a nondegenerate minimum -- far inside Newton's region of quadratic
+ * convergence around it -- and plain Newton steps (the Hessian there is
+ * positive definite; a CG that meets non-positive curvature is a failure)
+ * finish the solve until max_i |F_k(v)_i| / m_i <= ftol.
+ * stats = {pseudo-steps, Newton iterations, CG iterations}.  Returns the
+ * pseudo-steps taken, or -1.
+ */
+static int prox_cg(int n, const double* mass, const double* Kst, const or_level* lv,
+                   const double* w, double inv_tau, const double* G, double* d) {
+  int no = lv->dim == 3 ? 27 : 9, ctr = lv->dim == 3 ? 13 : 4;
+  double dt = lv->T / lv->m;
+  double* pinv = malloc(sizeof(double) * n);
+  double* r = malloc(sizeof(double) * n);
+  double* z = malloc(sizeof(double) * n);
+  double* p = malloc(sizeof(double) * n);
+  double* q = malloc(sizeof(double) * n);
+  for (int i = 0; i < n; ++i)
+    pinv[i] = 1.0 / (mass[i] * (inv_tau + 1.0 / dt - rxn_d(lv->c, lv->a, w[i])) +
+                     Kst[(size_t)i * no + ctr]);
+  memset(d, 0, sizeof(double) * n);
+  for (int i = 0; i < n; ++i) { r[i] = -G[i]; z[i] = pinv[i] * r[i]; p[i] = z[i]; }
+  double rz = dot(n, r, z), r0 = sqrt(rz);
+  int it = 0, ret = -1;
+  if (r0 == 0.0) { ret = 0; goto done; }
+  for (it = 1; it <= 20 * n + 100; ++it) {
+    hess_apply(lv, mass, Kst, w, p, q);
+    for (int i = 0; i < n; ++i) q[i] += mass[i] * inv_tau * p[i];
+    double pq = dot(n, p, q);
+    if (!(pq > 0.0)) break;   /* cannot happen for a positive definite Hessian */
+    double alpha = rz / pq;
+    for (int i = 0; i < n; ++i) { d[i] += alpha * p[i]; r[i] -= alpha * q[i]; z[i] = pinv[i] * r[i]; }
+    double rz_new = dot(n, r, z);
+    if (sqrt(rz_new) <= 1e-14 * r0) { ret = it; break; }
+    double beta = rz_new / rz;
+    for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    rz = rz_new;
+  }
+done:
+  free(pinv); free(r); free(z); free(p); free(q);
+  return ret;
+}
+
+int or_step_gradient_flow(const or_level* lv, const double* mass, const double* Kst,
+                          const double* up, const double* v0, double* u, double tau, double ftol,
+                          int max_pseudo, int* stats) {
+  int n = or_nodes(lv);
+  double dt = lv->T / lv->m;
+  double rmax = lv->c * ((1.0 + lv->a) * (1.0 + lv->a) / 3.0 - lv->a);
+  if (!(tau > 0.0) || tau * (rmax - 1.0 / dt) >= 1.0) return -1;   /* not strictly convex */
+  double* v = malloc(sizeof(double) * n);
+  double* F = malloc(sizeof(double) * n);
+  double* G = malloc(sizeof(double) * n);
+  double* d = malloc(sizeof(double) * n);
+  double* Ku = malloc(sizeof(double) * n);
+  double* Kd = malloc(sizeof(double) * n);
+  int j, ok = 0, newton = 0, cg = 0;
+  double inv_tau = 1.0 / tau;
+  memcpy(u, v0 ? v0 : up, sizeof(double) * n);
+  const double flow_tol = ftol > 1e-8 ? ftol : 1e-8;
+  for (j = 0; j <= max_pseudo; ++j) {
+    or_step_residual(lv, mass, Kst, u, up, F);
+    double fm = 0.0;
+    for (int i = 0; i < n; ++i) if (fabs(F[i]) / mass[i] > fm) fm = fabs(F[i]) / mass[i];
+    if (fm <= flow_tol) { ok = 1; break; }
+    if (j == max_pseudo) break;
+    memcpy(v, u, sizeof(double) * n);
+    /* Newton on the strictly convex pseudo-step objective
+       P(w) = E(w) + (w - v)^T M (w - v) / (2 tau),  gradient F(w) + M (w - v) / tau */
+    int conv = 0;
+    for (int it = 0; it < 100 && !conv; ++it) {
+      if (it > 0) or_step_residual(lv, mass, Kst, u, up, F);
+      for (int i = 0; i < n; ++i) G[i] = F[i] + mass[i] * inv_tau * (u[i] - v[i]);
+      int c1 = prox_cg(n, mass, Kst, lv, u, inv_tau, G, d);
+      if (c1 < 0) goto fail;
+      cg += c1;
+      ++newton;
+      double dmax = 0.0;
+      for (int i = 0; i < n; ++i) if (fabs(d[i]) > dmax) dmax = fabs(d[i]);
+      double alpha = 1.0;
+      if (dmax > 1e-8) {
+        double gd = dot(n, G, d);
+        or_stiff_apply(lv, Kst, u, Ku);
+        or_stiff_apply(lv, Kst, d, Kd);
+        for (int h = 0; h < 60; ++h) {
+          double dP = energy_change(lv, n, mass, u, up, d, Ku, Kd, alpha);
+          for (int i = 0; i < n; ++i) {
+            double w = alpha * d[i];
+            dP += mass[i] * w * (2.0 * (u[i] - v[i]) + w) * 0.5 * inv_tau;
+          }
+          if (dP <= 1e-4 * alpha * gd) break;
+          alpha *= 0.5;
+        }
+      }
+      for (int i = 0; i < n; ++i) u[i] += alpha * d[i];
+      if (dmax <= 1e-13) conv = 1;
+    }
+    if (!conv) goto fail;
+  }
+  if (ok && flow_tol > ftol) {
+    /* Newton polish at the nondegenerate minimum the flow has reached */
+    ok = 0;
+    for (int it = 0; it < 50; ++it) {
+      or_step_residual(lv, mass, Kst, u, up, F);
+      double fm = 0.0;
+      for (int i = 0; i < n; ++i) if (fabs(F[i]) / mass[i] > fm) fm = fabs(F[i]) / mass[i];
+      if (fm <= ftol) { ok = 1; break; }
+      int c1 = prox_cg(n, mass, Kst, lv, u, 0.0, F, d);
+      if (c1 < 0) break;
+      cg += c1;
+      ++newton;
+      for (int i = 0; i < n; ++i) u[i] += d[i];
+    }
+  }
+fail:
+  if (stats) { stats[0] = j; stats[1] = newton; stats[2] = cg; }
+  free(v); free(F); free(G); free(d); free(Ku); free(Kd);
+  return ok ? j : -1;
 }
 
 void or_activation(int nodes, int m, double dt, double T, const double* slab, double* t_act) {

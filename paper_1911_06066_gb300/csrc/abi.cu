@@ -46,7 +46,7 @@ mlmc_status mlmc::cuda_fail(mlmc_ctx* ctx, cudaError_t e, const char* where) {
 // indefinite: c dt max r' <= mixed_cdr_max (default 2), max r' =
 // c((1+a)^2/3 - a).  On strongly indefinite levels the negative-curvature
 // decisions of an FP32 CG can pick a different root than FP64.
-static bool level_mixed(const mlmc_config& c, const LevelDesc& lv) {
+bool mlmc::level_mixed(const mlmc_config& c, const LevelDesc& lv) {
   if (c.precision != MLMC_PREC_MIXED) return false;
   double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
   double lim = c.mixed_cdr_max > 0.0 ? c.mixed_cdr_max : 2.0;
@@ -68,11 +68,7 @@ static bool level_gmg(const mlmc_config& c, const LevelDesc& lv, MGDesc* mg) {
   return true;
 }
 
-struct SolveWs {
-  size_t coef64, coef32, ubuf, F, Ku, Kd, kr, mg, total;
-};
-
-static SolveWs solve_ws(const mlmc_config& c, const LevelDesc& lv, int n, bool mixed) {
+SolveWs mlmc::solve_ws(const mlmc_config& c, const LevelDesc& lv, int n, bool mixed) {
   SolveWs w;
   size_t N = (size_t)lv.nodes, NO = (size_t)n_offsets(lv.dim), kr = mixed ? 4 : 8;
   MGDesc mg;
@@ -119,6 +115,67 @@ static bool check_ws(mlmc_ctx* ctx, void* ws, size_t have, size_t need) {
   return true;
 }
 
+// Geometry of level `level` of a configuration: n0[d] 2^level cells per axis,
+// m0 2^level implicit-Euler steps.  False (and a message) when a size does not
+// fit the kernels' index types.
+bool mlmc::derive_level(const mlmc_config& c, int level, LevelDesc* out, std::string* err) {
+  LevelDesc lv;
+  lv.dim = c.dim;
+  int64_t nodes = 1, cells = 1;
+  double vol = 1.0;
+  if (level < 0 || level >= MLMC_MAX_LEVELS) { *err = "level out of range"; return false; }
+  for (int d = 0; d < 3; ++d) {
+    if (d < c.dim) {
+      if (c.n0[d] < 1 || !(c.L[d] > 0.0)) { *err = "n0 and L must be positive"; return false; }
+      int64_t nn = (int64_t)c.n0[d] << level;
+      if (nn > (1 << 20)) { *err = "grid too large"; return false; }
+      lv.n[d] = (int)nn; lv.N[d] = (int)nn + 1; lv.h[d] = c.L[d] / (double)nn;
+    } else {
+      lv.n[d] = 1; lv.N[d] = 1; lv.h[d] = 1.0;
+    }
+    nodes *= lv.N[d]; cells *= lv.n[d]; vol *= (d < c.dim ? lv.h[d] : 1.0);
+  }
+  if (nodes > (int64_t)1 << 31) { *err = "grid too large"; return false; }
+  const int64_t m = (int64_t)c.m0 << level;
+  if (c.m0 < 1 || m > (int64_t)1 << 30) { *err = "time steps out of range"; return false; }
+  lv.nodes = nodes; lv.cells = cells; lv.vol = vol;
+  lv.m = (int)m;
+  lv.T = c.T;
+  lv.dt = c.T / (double)lv.m;
+  *out = lv;
+  return true;
+}
+
+void mlmc::derive_physics(const mlmc_config& c, Physics* out) {
+  const double pi = 3.141592653589793238462643;
+  Physics ph;
+  ph.stim_ps = nullptr;
+  ph.c = c.c; ph.a = c.a; ph.s_t = c.s_t; ph.s_l0 = c.s_l0;
+  ph.th0 = c.theta0_deg * pi / 180.0;
+  ph.th1 = c.theta1_deg * pi / 180.0;
+  ph.Lz = c.dim == 3 ? c.L[2] : 1.0;
+  ph.stim_r2 = c.stim_r * c.stim_r;
+  for (int d = 0; d < 3; ++d) ph.stim_c[d] = c.stim_c[d];
+  *out = ph;
+}
+
+// Solver parameters of one level: the configured tolerances (the FP32 inner
+// solves no tighter than 1e-5), the root-selection regime of the level
+// (gradient-flow continuation where a step has several roots) and the FP32
+// range scaling of the fine 3D levels.
+SolverParams mlmc::level_solver_params(const mlmc_config& c, const LevelDesc& lv, bool mixed) {
+  SolverParams sp;
+  sp.newton_tol = c.newton_tol;
+  sp.newton_max = c.newton_max;
+  sp.lin_rtol = mixed ? fmax(c.lin_rtol, 1e-5) : c.lin_rtol;
+  sp.lin_max = c.lin_max;
+  sp.ls_full_step = 1e-6;
+  sp.flow = level_has_several_roots(c.c, c.a, lv.dt) ? 1 : 0;
+  sp.tau0 = 0.5 / (c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a));
+  sp.cg_scale = mixed && cg_needs_scaling(lv) ? 1 : 0;
+  return sp;
+}
+
 // --------------------------------------------------------------- create
 extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   if (!out) return fail(nullptr, MLMC_ERR_ARG, "out is NULL");
@@ -152,44 +209,13 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   ctx->cfg = c;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e != cudaSuccess) { delete ctx; return fail(nullptr, MLMC_ERR_CUDA, cudaGetErrorString(e)); }
-  const double pi = 3.141592653589793238462643;
   for (int l = 0; l < c.n_levels; ++l) {
-    LevelDesc& lv = ctx->lv[l];
-    lv.dim = c.dim;
-    int64_t nodes = 1, cells = 1;
-    double vol = 1.0;
-    for (int d = 0; d < 3; ++d) {
-      if (d < c.dim) {
-        int64_t nn = (int64_t)c.n0[d] << l;
-        if (nn > (1 << 20)) { delete ctx; return fail(nullptr, MLMC_ERR_ARG, "grid too large"); }
-        lv.n[d] = (int)nn; lv.N[d] = (int)nn + 1; lv.h[d] = c.L[d] / (double)nn;
-      } else {
-        lv.n[d] = 1; lv.N[d] = 1; lv.h[d] = 1.0;
-      }
-      nodes *= lv.N[d]; cells *= lv.n[d]; vol *= (d < c.dim ? lv.h[d] : 1.0);
-    }
-    if (nodes > (int64_t)1 << 31) { delete ctx; return fail(nullptr, MLMC_ERR_ARG, "grid too large"); }
-    lv.nodes = nodes; lv.cells = cells; lv.vol = vol;
-    lv.m = (int)((int64_t)c.m0 << l);
-    lv.T = c.T;
-    lv.dt = c.T / (double)lv.m;
+    std::string why;
+    if (!derive_level(c, l, &ctx->lv[l], &why)) { delete ctx; return fail(nullptr, MLMC_ERR_ARG, why); }
   }
-  Physics& ph = ctx->ph;
-  ph.stim_ps = nullptr;
-  ph.c = c.c; ph.a = c.a; ph.s_t = c.s_t; ph.s_l0 = c.s_l0;
-  ph.th0 = c.theta0_deg * pi / 180.0;
-  ph.th1 = c.theta1_deg * pi / 180.0;
-  ph.Lz = c.dim == 3 ? c.L[2] : 1.0;
-  ph.stim_r2 = c.stim_r * c.stim_r;
-  for (int d = 0; d < 3; ++d) ph.stim_c[d] = c.stim_c[d];
+  derive_physics(c, &ctx->ph);
   SolverParams& sp = ctx->sp;
-  sp.newton_tol = c.newton_tol;
-  sp.newton_max = c.newton_max;
-  sp.lin_rtol = c.precision == MLMC_PREC_MIXED ? fmax(c.lin_rtol, 1e-5) : c.lin_rtol;
-  sp.lin_max = c.lin_max;
-  sp.ls_full_step = 1e-6;
-  sp.step_max = __builtin_huge_val();   // set per level in solve_into
-  sp.cg_scale = 0;                      // likewise
+  sp = level_solver_params(c, ctx->lv[0], c.precision == MLMC_PREC_MIXED);   // per level in solve_into
 
   // KL mode table and per-level 1D mode values at the cell centroids
   ctx->M = c.kl_modes;
@@ -416,10 +442,7 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     ctx->ev_level.push_back(ctx->prof_level);
     CK(ctx, cudaEventRecordWithFlags(e0, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  SolverParams sp = ctx->sp;
-  sp.lin_rtol = mixed ? fmax(ctx->cfg.lin_rtol, 1e-5) : ctx->cfg.lin_rtol;
-  sp.step_max = step_limit(ctx->cfg.c, ctx->cfg.a, lv.dt);
-  sp.cg_scale = mixed && cg_needs_scaling(lv) ? 1 : 0;
+  const SolverParams sp = level_solver_params(ctx->cfg, lv, mixed);
   if (use_cluster) {
     ClusterGlobal g;
     g.u = (double*)(ws + w.ubuf);

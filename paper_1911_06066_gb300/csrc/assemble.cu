@@ -101,4 +101,10 @@ cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double
   return cudaGetLastError();
 }
 
+cudaError_t preload_assemble() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, assemble_kernel<2>);
+  return e == cudaSuccess ? cudaFuncGetAttributes(&a, assemble_kernel<3>) : e;
+}
+
 }  // namespace mlmc

@@ -1,5 +1,5 @@
 // Rows a9-a10: level-pair differences of the activation map on the coarsest
-// grid and the MC / MLMC estimators (Sec. 2.2, Eq. MC-estimator and
+// grid and the MC / MLMC estimators (Sec. 3.1.2, Eq. MC-estimator and
 // Eq. MLMC-estimator, u_{-1} = 0).
 //
 // Transfer (Sec. 3.4): the grids are vertex-nested, so a nodal field of level

@@ -41,9 +41,48 @@ struct SolverParams {
   double lin_rtol;
   int lin_max;
   double ls_full_step;   // max|d| below which the full Newton step is taken
-  double step_max;       // largest nodal move per Newton iteration (inf: none)
+  int flow;              // the level's steps have several roots (c dt max r' > 1):
+                         // gradient-flow continuation instead of Newton-CG
+  double tau0;           // first pseudo-step of the continuation, 1 / (2 max r')
   int cg_scale;          // FP32 CG: solve for a power-of-two scaled right-hand side
 };
+
+// Gradient-flow continuation (levels with c dt max r' > 1; max r' =
+// c((1+a)^2/3 - a)).  Such a step has several roots; the root is the end
+// point of the gradient flow M v' = -F(v) of the step energy from u_{k-1},
+// the local minimum in whose basin u_{k-1} lies.  It is reached by linearly
+// implicit pseudo-steps (M/t + H(u)) d = -F(u): t starts at tau0, doubles
+// after each accepted step and is capped at FLOW_CAP / max_i (r'(u_i) - 1/dt),
+// which keeps M/t + H positive definite, so that a step never reverses the
+// flow's unstable component near a saddle; a step moving a node by more than
+// FLOW_MOVE is retried shorter; once an accepted step moves no node by more
+// than the switch threshold (FLOW_NEWTON at first) Newton steps finish the
+// solve while their CG meets only positive curvature and they move no node by
+// more than 10x the threshold (else the flow resumes with a 10x smaller
+// threshold).
+constexpr double FLOW_CAP = 0.5;
+constexpr double FLOW_MOVE = 0.3;
+constexpr double FLOW_TMIN = 1e-9;
+constexpr double FLOW_TMAX = 1e20;
+constexpr double FLOW_NEWTON = 1e-2;
+inline bool level_has_several_roots(double c, double a, double dt) {
+  return dt * c * ((1.0 + a) * (1.0 + a) / 3.0 - a) > 1.0;
+}
+
+// Configuration-derived quantities shared by mlmc_create, mlmc_solve and
+// mlmc_solve_noalloc (defined in abi.cu).
+bool derive_level(const mlmc_config& c, int level, LevelDesc* lv, std::string* err);
+void derive_physics(const mlmc_config& c, Physics* ph);
+// FP32 inner solves are used only where the step Jacobian is at most mildly
+// indefinite: MLMC_PREC_MIXED and c dt max r' <= mixed_cdr_max (default 2).
+bool level_mixed(const mlmc_config& c, const LevelDesc& lv);
+SolverParams level_solver_params(const mlmc_config& c, const LevelDesc& lv, bool mixed);
+// Byte offsets of one level's solver scratch for n samples (the workspace of
+// mlmc_solve), 256-byte aligned.
+struct SolveWs {
+  size_t coef64, coef32, ubuf, F, Ku, Kd, kr, mg, total;
+};
+SolveWs solve_ws(const mlmc_config& c, const LevelDesc& lv, int n, bool mixed);
 
 // FP32 inner solves on grids whose lumped mass per time step is this small
 // (the fine 3D levels) scale the CG's right-hand side by a power of two: their
@@ -76,14 +115,6 @@ struct MGDesc {
 // Builds the hierarchy of grid lv: coarsen while some axis has an even cell
 // count and the grid has more than 512 nodes.
 void mg_hierarchy(const LevelDesc& lv, int nu, int coarse_sweeps, MGDesc* mg);
-
-// Root-selection step limit: on strongly indefinite steps (c dt max r' > 2,
-// max r' = c((1+a)^2/3 - a)) no node moves by more than 0.1 per Newton
-// iteration; elsewhere steps are not limited.
-inline double step_limit(double c, double a, double dt) {
-  double rmax = c * ((1.0 + a) * (1.0 + a) / 3.0 - a);
-  return dt * rmax > 2.0 ? 0.1 : __builtin_huge_val();
-}
 
 // Number of stencil couplings per node (3^dim) and the centre index.
 __host__ __device__ inline int n_offsets(int dim) { return dim == 3 ? 27 : 9; }
@@ -131,6 +162,8 @@ cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_la
 cudaError_t preload_kl_tc();
 cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,
                             double* coef64, float* coef32, cudaStream_t st);
+// Loads the assembly kernels' module (both dimensions) without launching.
+cudaError_t preload_assemble();
 cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                          bool mixed, int n, const double* coef64, const float* coef32,
                          double* slab, double* ubuf, double* F, double* Ku, double* Kd,

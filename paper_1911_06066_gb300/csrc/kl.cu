@@ -1,4 +1,4 @@
-// Row a2: the truncated Karhunen-Loeve field Z (Sec. 2.2, Eq. KL-expansion and
+// Row a2: the truncated Karhunen-Loeve field Z (Sec. 3.1.1, Eq. KL-expansion and
 // Eq. KL-expansion-deterministic) for the separable exponential covariance
 //   k(x, y) = sigma2 prod_d exp(-|x_d - y_d| / ell).
 // The multi-dimensional eigenpairs are products of 1D eigenpairs, which have a

@@ -1,4 +1,4 @@
-// Row a2 in the mixed-precision path: the truncated KL field (Sec. 2.2,
+// Row a2 in the mixed-precision path: the truncated KL field (Sec. 3.1.1,
 // Eq. KL-expansion-deterministic)
 //   Z[s][cell] = sum_q phi_q(centroid) * (sqrt(lam_q) xi[s][q])
 // as one dense contraction (cells x modes) . (modes x samples) on the fifth-

@@ -1,4 +1,4 @@
-// Row a1: the KL random inputs xi (Sec. 2.2, Eq. KL-expansion-deterministic;
+// Row a1: the KL random inputs xi (Sec. 3.1.1, Eq. KL-expansion-deterministic;
 // here xi_k ~ N(0,1)), drawn from a counter-based stream so that any sample of
 // any level can be generated independently and reproduced bit for bit.
 //

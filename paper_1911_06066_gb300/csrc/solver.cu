@@ -9,20 +9,25 @@
 // Its Jacobian block H = M/dt + K - M diag(r'(u)) is symmetric -- F_k is the
 // gradient of the step energy
 //   E(u) = (u-u_{k-1})^T M (u-u_{k-1})/(2dt) + u^T K u/2 - sum_i M_i R(u_i),  R' = r
-// -- and indefinite when c dt max r' > 1, where the step has several roots.
-// The root is the one line-search Newton-CG on E reaches from u_{k-1}
-// (Nocedal & Wright, Numerical Optimization, Alg. 7.1):
-//   * d from CG with the Jacobi preconditioner |diag H| on H d = -F, from 0,
-//     until the preconditioned residual drops by lin_rtol, truncated at the
-//     first direction with p^T H p <= 0 (then the current iterate, or the
-//     preconditioned steepest-descent step in the first iteration);
-//   * stop once max|d| <= newton_tol (d still applied);
-//   * on strongly indefinite steps (c dt max r' > 2) start from
-//     alpha = min(1, 0.1 / max|d|), so no node moves by more than 0.1 per
-//     iteration and the selected root does not depend on rounding;
-//   * otherwise Armijo backtracking on E (sigma = 1e-4, halving, at most 40),
-//     the energy change summed node by node in a cancellation-free form; the
-//     full step is taken when max|d| <= ls_full_step.
+// -- and indefinite when c dt max r' > 1, where the step has several roots
+// (local minima of E).  The root is the end point of the gradient flow
+// M v' = -F_k(v) from u_{k-1}: the minimum in whose basin u_{k-1} lies.
+//   * Levels with several roots (sp.flow): gradient-flow continuation by
+//     linearly implicit pseudo-steps (M/t + H(u)) d = -F(u), u += d, with the
+//     pseudo-step t growing x2 per accepted step from 1/(2 max r'), capped at
+//     FLOW_CAP / max_i (r'(u_i) - 1/dt) so that M/t + H stays positive
+//     definite, retried shorter when it would move a node by more than
+//     FLOW_MOVE, and finished by Newton steps (t = infinity) once the flow
+//     has nearly arrived (see SolverParams in internal.cuh).
+//   * Other levels: H is positive definite for every state and the root
+//     unique; Newton with Armijo backtracking on E (sigma = 1e-4, halving, at
+//     most 40; the energy change summed node by node in a cancellation-free
+//     form; full step when max|d| <= ls_full_step).
+//   * Linear solves by CG with the Jacobi preconditioner |diag|, from 0,
+//     until the preconditioned residual drops by lin_rtol; truncated at the
+//     first direction with p^T A p <= 0 (then the current iterate, or the
+//     preconditioned steepest-descent step in the first iteration).
+//   * Stop once an accepted step moves no node by more than newton_tol.
 //
 // GPU mapping: one thread block per sample; every block loops over all time
 // steps, Newton and CG iterations on its own, so the whole slab of a batch is
@@ -144,13 +149,31 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
   for (int step = 1; step <= lv.m; ++step) {
     const double* up = sl ? sl + (int64_t)(step - 1) * N : ub + (int64_t)((step - 1) & 1) * N;
     double* u = sl ? sl + (int64_t)step * N : ub + (int64_t)(step & 1) * N;
-    for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) u[A] = up[A];
-    __syncthreads();
+    double smax = 0.0;   // max_i (r'(u_i) - 1/dt), clipped at 0 (continuation levels)
+    {
+      double s_loc = 0.0;
+      for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {
+        const double ua = up[A];
+        u[A] = ua;
+        s_loc = fmax(s_loc, rxn_d(ph, ua) - inv_dt);
+      }
+      smax = block_max(s_loc, sh);   // also publishes u
+    }
+    double tau = sp.tau0, sw = FLOW_NEWTON;
+    bool newton_phase = false;
     bool conv = false, lin_fail = false;
     int it;
     for (it = 1; it <= sp.newton_max; ++it) {
-      // residual, Hessian diagonal, CG start (r = -F, z = P^-1 r, p = z, d = 0)
-      double rz_loc = 0.0;
+      double t = tau;
+      if (sp.flow && !newton_phase && smax > 0.0 && t > FLOW_CAP / smax) t = FLOW_CAP / smax;
+      const double shift = sp.flow && !newton_phase ? 1.0 / t : 0.0;
+      // residual, Hessian diagonal, CG start (r = -F, z = P^-1 r, p = z, d = 0).
+      // FP32 CG on grids with a tiny lumped mass per time step (sp.cg_scale):
+      // the right-hand side is scaled by the power of two sigma with
+      // ||F||_2 sigma in [1, 2) and d by 1/sigma after the solve (exact), so
+      // that the CG's products stay in FP32's normal range.
+      const bool SCALE = sizeof(KR) == 4 && sp.cg_scale != 0;
+      double rz_loc = 0.0, f2_loc = 0.0;
       for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {
         int i, j, k;
         node_ijk(lv, A, i, j, k);
@@ -160,7 +183,7 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
         Ku[A] = ku;
         double f = ku + mA * inv_dt * (uA - up[A]) - mA * rxn(ph, uA);
         F[A] = f;
-        double hmA = mA / dt - mA * rxn_d(ph, uA);
+        double hmA = mA * (inv_dt + shift) - mA * rxn_d(ph, uA);
         double pv = 1.0 / fabs(hmA + c64[(int64_t)centre_offset(DIM) * N + A]);
         KR rv = (KR)(-f);
         KR zv = (KR)pv * rv;
@@ -168,6 +191,19 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
         pinv[A] = (KR)pv;
         r[A] = rv; z[A] = zv; p[A] = zv; d[A] = (KR)0;
         rz_loc += (double)(rv * zv);
+        f2_loc += f * f;
+      }
+      double sigma = 1.0;
+      if (SCALE) {
+        const double f2 = block_sum(f2_loc, sh);
+        if (f2 > 0.0) sigma = ldexp(1.0, -ilogb(sqrt(f2)));
+        rz_loc = 0.0;
+        for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {
+          const KR rv = (KR)(-F[A] * sigma);
+          const KR zv = pinv[A] * rv;
+          r[A] = rv; z[A] = zv; p[A] = zv;
+          rz_loc += (double)(rv * zv);
+        }
       }
       double rz = block_sum(rz_loc, sh);
       const double r0 = sqrt(rz);
@@ -212,25 +248,39 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
       cg_total += cg;
       trunc_total += truncated ? 1 : 0;
       if (lin_fail) break;
+      if (SCALE && sigma != 1.0) {
+        const KR inv_sigma = (KR)(1.0 / sigma);   // a power of two: exact
+        for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) d[A] *= inv_sigma;
+        __syncthreads();
+      }
       double dmax_loc = 0.0;
       for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) dmax_loc = fmax(dmax_loc, fabs((double)d[A]));
       const double dmax = block_max(dmax_loc, sh);
-      double alpha = 1.0;
-      if (dmax > sp.step_max) {
-        // max-norm trust region: clip every component, or scale the whole
-        // direction if the clipped one is not a descent direction
-        const KR lim = (KR)sp.step_max;
-        double gdc_loc = 0.0;
-        for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS)
-          gdc_loc += F[A] * (double)fmin(fmax(d[A], -lim), lim);
-        const double gdc = block_sum(gdc_loc, sh);
-        if (gdc < 0.0) {
-          for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) d[A] = fmin(fmax(d[A], -lim), lim);
-          __syncthreads();
+      if (sp.flow) {
+        bool accept;
+        if (newton_phase) {
+          accept = !(truncated || dmax > 10.0 * sw);
+          if (!accept) { newton_phase = false; sw *= 0.1; ++halvings; }
         } else {
-          alpha = sp.step_max / dmax;
+          accept = !(dmax > FLOW_MOVE && t > FLOW_TMIN);
+          if (!accept) { tau = t * 0.5 * FLOW_MOVE / dmax; ++halvings; }
         }
+        if (!accept) continue;       // the state is unchanged; retry
+        double s_loc = 0.0;
+        for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {
+          const double un = u[A] + (double)d[A];
+          u[A] = un;
+          s_loc = fmax(s_loc, rxn_d(ph, un) - inv_dt);
+        }
+        smax = block_max(s_loc, sh);
+        if (dmax <= sp.newton_tol) { conv = true; break; }
+        if (!newton_phase) {
+          if (dmax <= sw) newton_phase = true;
+          tau = fmin(2.0 * t, FLOW_TMAX);
+        }
+        continue;
       }
+      double alpha = 1.0;
       if (dmax > sp.newton_tol && dmax > sp.ls_full_step) {
         double gd_loc = 0.0;
         for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {

@@ -362,11 +362,35 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     double* u = (step & 1) ? ubuf1 : ubuf0;
     const double* up = (step & 1) ? ubuf0 : ubuf1;
     const View<double>& uv = (step & 1) ? uv1 : uv0;
-    for (int a = tid; a < b.nb; a += NT) u[a] = up[a];
-    cluster_barrier(cl, b.C);
+    // On levels whose steps have several roots (sp.flow) the step follows the
+    // gradient-flow continuation (see SolverParams): smax = max_i (r'(u_i) -
+    // 1/dt), clipped at 0, of the current state caps the pseudo-step.
+    double smax = 0.0;
+    {
+      double s_loc = 0.0;
+      for (int a = tid; a < b.nb; a += NT) {
+        const double ua = up[a];
+        u[a] = ua;
+        if (sp.flow) s_loc = fmax(s_loc, rxn_d(ph, ua) - inv_dt);
+      }
+      if (sp.flow) {
+        double v1[1] = {s_loc};
+        cluster_reduce<NT, double, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+        smax = bc[0];
+      } else {
+        cluster_barrier(cl, b.C);
+      }
+    }
+    double tau = sp.tau0, sw = FLOW_NEWTON;
+    bool newton_phase = false;
     bool conv = false, lin_fail = false;
     int it;
     for (it = 1; it <= sp.newton_max; ++it) {
+      // pseudo-step of the continuation (shift = M/t on the Hessian diagonal),
+      // or a Newton step (shift 0)
+      double t = tau;
+      if (sp.flow && !newton_phase && smax > 0.0 && t > FLOW_CAP / smax) t = FLOW_CAP / smax;
+      const double shift = sp.flow && !newton_phase ? 1.0 / t : 0.0;
       // residual, Hessian diagonal and the CG start r = -F, z = P^-1 r, p = z, d = 0
       // FP32 CG on grids with a tiny lumped mass per time step (sp.cg_scale,
       // the fine 3D levels): the right-hand side is scaled by a power of two
@@ -393,7 +417,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         // the only user); no FP64 division on the per-node path
         const KR uK = (KR)uA, mK = (KR)mA;
         const KR rdK = (KR)ph.c * ((KR)(-3.0) * uK * uK + (KR)(2.0 * (1.0 + ph.a)) * uK - (KR)ph.a);
-        const KR hmA = mK * ((KR)inv_dt - rdK);
+        const KR hmA = mK * ((KR)(inv_dt + shift) - rdK);
         hm[a] = hmA;
         d[a] = (KR)0;
         const KR pvv = MG ? (KR)1 / (fabs(hmA) + mgb[mg.l[0].ks + A])   // l1-Jacobi (V-cycle smoother)
@@ -535,21 +559,35 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         cluster_reduce<NT, KR, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
       }
       const double dmax = bc[0];
-      double alpha = 1.0;
-      if (dmax > sp.step_max) {
-        // max-norm trust region: clip every component, or scale the whole
-        // direction if the clipped one is not a descent direction
-        const KR lim = (KR)sp.step_max;
-        double g1[1] = {0.0};
-        for (int a = tid; a < b.nb; a += NT) g1[0] += F[a] * (double)fmin(fmax(d[a], -lim), lim);
-        cluster_reduce<NT, double, 1>(g1, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
-        if (bc[0] < 0.0) {
-          for (int a = tid; a < b.nb; a += NT) d[a] = fmin(fmax(d[a], -lim), lim);
-          cluster_barrier(cl, b.C);
+      if (sp.flow) {
+        bool accept;
+        if (newton_phase) {
+          accept = !(truncated || dmax > 10.0 * sw);
+          if (!accept) { newton_phase = false; sw *= 0.1; ++halvings; }
         } else {
-          alpha = sp.step_max / dmax;
+          accept = !(dmax > FLOW_MOVE && t > FLOW_TMIN);
+          if (!accept) { tau = t * 0.5 * FLOW_MOVE / dmax; ++halvings; }
         }
+        if (!accept) continue;       // the state is unchanged; retry
+        double s_loc = 0.0;
+        for (int a = tid; a < b.nb; a += NT) {
+          const double un = u[a] + (double)d[a];
+          u[a] = un;
+          s_loc = fmax(s_loc, rxn_d(ph, un) - inv_dt);
+        }
+        {
+          double v1[1] = {s_loc};
+          cluster_reduce<NT, double, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+          smax = bc[0];
+        }
+        if (dmax <= sp.newton_tol) { conv = true; break; }
+        if (!newton_phase) {
+          if (dmax <= sw) newton_phase = true;
+          tau = fmin(2.0 * t, FLOW_TMAX);
+        }
+        continue;
       }
+      double alpha = 1.0;
       if (dmax > sp.newton_tol && dmax > sp.ls_full_step) {
         // The step energy is a quartic polynomial in the step length (R is a
         // quartic), so for every trial length al
@@ -573,7 +611,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           v4[2] += mA * r2 * d2 * da;
           v4[3] += mA * d2 * d2;
         }
-        const double alpha0 = alpha, cc = ph.c;
+        const double alpha0 = alpha, cc = ph.c;   // alpha0 = 1
         cluster_reduce<NT, double, 4>(v4, 0, red, slot, bc, par, cl, b.C, b.rank,
                                       [=](double* o) {
                                         const double gd = o[0], dHd = o[1];

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Karhunen-Loeve expansion (Sec. 2.2, Eq. KL-expansion)
+"""Pins of the oracle's Karhunen-Loeve expansion (Sec. 3.1.1, Eq. KL-expansion)
 for the separable exponential covariance: closed-form eigenpairs against a
 Nystrom eigen-solve of the kernel, the trace identity, orthonormality, the
 mode ordering and the covariance of the synthesised field."""

@@ -1,5 +1,5 @@
 """Pins of the oracle's activation-time QoI, grid transfer and the MC / MLMC
-estimators (Sec. 2.2, Eq. MC-estimator and Eq. MLMC-estimator)."""
+estimators (Sec. 3.1.2, Eq. MC-estimator and Eq. MLMC-estimator)."""
 import math
 
 import numpy as np

@@ -1,6 +1,6 @@
 """Pins of the oracle's generator: Philox4x32-10 known answers, the own ln and
 sin/cos against the C library, and the distribution of the Box-Muller normals
-(the KL inputs xi of Sec. 2.2, drawn from a counter-based Philox stream)."""
+(the KL inputs xi of Sec. 3.1.1, drawn from a counter-based Philox stream)."""
 import math
 
 import numpy as np

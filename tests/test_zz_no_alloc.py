@@ -59,6 +59,31 @@ def test_noalloc_matches_workspace_solve_twice():
         ctx.close()
 
 
+def test_noalloc_allocates_nothing_after_setup():
+    """The defining property: once the first call on the device has done its
+    one-time set-up, a call changes neither the device's free memory nor
+    torch's allocation count."""
+    w = W.MLMC2D_3LVL
+    cfg = B.make_config(w, B.MLMC_PREC_MIXED)
+    ctx = B.Context(B.make_config(w, B.MLMC_PREC_MIXED, solver=B.MLMC_SOLVER_BLOCK))
+    Z = ctx.kl_field(1, ctx.xi(3, 1, torch.tensor([0, 1, 2])))
+    nodes = ctx.level_info(1)[0]
+    t = torch.zeros((3, nodes), dtype=torch.float64, device="cuda")
+    info = torch.zeros((3, 8), dtype=torch.int32, device="cuda")
+    assert noalloc(cfg, 1, Z, t, info) == B.MLMC_OK            # set-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    assert noalloc(cfg, 1, Z, t, info) == B.MLMC_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    allocs1 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    assert free1 == free0, (free0, free1)
+    assert allocs1 == allocs0
+    assert all(i["status"] == 0 for i in B.info_dicts(info))
+    ctx.close()
+
+
 def test_noalloc_rejects_oversize_requests():
     cfg = B.make_config(W.MLMC2D_3LVL)
     Z = torch.zeros((64, 128 * 128), dtype=torch.float64, device="cuda")
@@ -69,3 +94,7 @@ def test_noalloc_rejects_oversize_requests():
     msg = B.lib().mlmc_last_error(None).decode()
     assert "mlmc_solve_noalloc" in msg and "scratch" in msg
     assert torch.count_nonzero(t).item() == 0          # nothing was launched
+    # a grid far beyond the array: refused by the size bound, before any
+    # product of sizes could wrap around
+    big = B.make_config(dict(W.MLMC2D_3LVL, n0=(1 << 19, 1 << 19)))
+    assert noalloc(big, 0, Z, t, info) in (-1, -6)
