@@ -32,14 +32,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-RMSE eps (s) for MLMC mean activation map; stencil HBM GB/s; p99 latency"
-# FP64 FMA throughput measured on this GB300 with independent FMA chains
-# (152 SMs; 2 FP64 FMA per clock per SM nominally = 1.26 TFLOP/s at 2.07 GHz).
-# FP64 runs at 1/74 of the FP32 rate on this part, so the FP64 pipe is the ALU
-# bound of the per-sample solve; FP32 work is not counted against it.
-FP64_PEAK_TFLOPS = 1.01
-# Algorithmic FP64 flops per node: one FP64 CG iteration (9-coupling stencil
-# and Hessian diagonal 20, two dots 4, four vector updates 7) and one Newton
-# iteration (residual: stencil 18, mass and reaction terms 12; update 2).
+# The ALU peaks are measured in-line by the library's FMA-chain probe
+# (mlmc_probe_fma_rate: 8 independent FMA chains per thread, 16 x 256 threads
+# per SM, CUDA events) and reported in the line; FP64 runs far below FP32 on
+# this part, so FP64 and FP32 work are each set against their own peak.
+# Algorithmic flops per node: one CG iteration (9-coupling stencil and Hessian
+# diagonal 20, two dots 4, four vector updates 7) and one nonlinear iteration
+# (residual: stencil 18, mass and reaction terms 12; update 2), in the CG's
+# precision and in FP64 respectively.
 FLOP_CG_NODE = 31
 FLOP_NEWTON_NODE = 32
 # DRAM bytes (read + write) per solve launch of one estimate of the 3-level 2D
@@ -308,14 +308,30 @@ def run_ours(args, w):
         if world > 1:
             torch.distributed.barrier()
 
+    # ALU peaks of this device, measured in-line (FMA-chain probe)
+    peaks = {"fp64_tflops": B.fma_rate(True, stream), "fp32_tflops": B.fma_rate(False, stream)}
+
+    from paper_1911_06066_gb300 import distributed as D
+
+    def one_estimate():
+        """One step: one whole MLMC estimate.  One rank: mlmc_run.  N ranks:
+        each rank runs its shard of every level's ids (mlmc_run_more), the
+        per-level states are all-gathered over NCCL and merged in rank order
+        (mlmc_merge_states); every rank ends with the estimate of all N_l."""
+        if world == 1:
+            return ctx.run(w["N"], seed=seed, batch=batch)
+        out = D.run_sharded(ctx, w["N"], seed=seed, batch=batch)
+        out["stats"] = None
+        return out
+
     warmup = max(args.warmup, 3) if w["dim"] == 2 else args.warmup
     for _ in range(warmup):
-        ctx.run(w["N"], seed=seed, batch=batch)
+        one_estimate()
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
-    dev_ms, wall_s, solve_ms, cg64_ni, nw_ni, launches, nsolve, rmse = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, []
-    cg_ni = 0.0
+    dev_ms, wall_s, solve_ms, launches, nsolve, rmse = 0.0, 0.0, 0.0, 0.0, 0.0, []
+    per_level = None
     for k in range(args.steps):
         flush.zero_()                       # L2 flush (512 MB > 126 MB L2) outside the timed span
         torch.cuda.synchronize()
@@ -323,26 +339,33 @@ def run_ours(args, w):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         e0.record(stream)
-        res = ctx.run(w["N"], seed=seed, batch=batch)     # host in, host out (synchronising)
+        res = one_estimate()                # host in, host out (synchronising)
         e1.record(stream)
         t1 = time.perf_counter()
         torch.cuda.synchronize()
         dev_ms += e0.elapsed_time(e1)
         wall_s += t1 - t0
         st = res["stats"]
-        solve_ms += st["solve_ms"]
-        cg64_ni += st["cg64_node_iters"]
-        cg_ni += st["cg_node_iters"]
-        nw_ni += st["newton_node_iters"]
-        launches += st["launches"]
-        nsolve += st["solve_launches"]
+        if st is not None:
+            solve_ms += st["solve_ms"]
+            launches += st["launches"]
+            nsolve += st["solve_launches"]
         rmse.append(res["rmse"])
+        # per grid level: the solve launches of this run and the counters since
+        # its reset (mlmc_run resets), i.e. this estimate's work
+        lv_stats = ctx.level_stats()
+        if per_level is None:
+            per_level = [dict(v) for v in lv_stats]
+        else:
+            for acc, v in zip(per_level, lv_stats):
+                for key in acc:
+                    acc[key] += v[key]
     torch.cuda.synchronize()
     clk = clocks.stop()
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = run_extras(w, B, prec, seed)
+        extras = run_extras(w, B, prec, seed, stream, peaks)
 
     ms = dev_ms / args.steps
     e2e_s = wall_s / args.steps
@@ -353,20 +376,18 @@ def run_ours(args, w):
         ms, e2e_s = t[0].item(), t[1].item()
     if rank != 0:
         return
-    flops = FLOP_CG_NODE * cg64_ni + FLOP_NEWTON_NODE * nw_ni
-    # per launch: flops per launch / mean launch duration (launches overlap);
-    # aggregate: all solve flops over the step's device time
-    achieved = flops / (solve_ms * 1e-3) / 1e12 if solve_ms > 0 else 0.0
-    aggregate = flops / (dev_ms * 1e-3) / 1e12 if dev_ms > 0 else 0.0
     L = w["levels"]
     n0 = (w["n0"][0] + 1) * (w["n0"][1] + 1) * ((w["n0"][2] + 1) if w["dim"] == 3 else 1)
     d2h = 8 * (2 * n0 + 2 * L * n0 + L + 2) + 8 * 5
+    levels = level_bounds(per_level, args.steps, peaks)
+    if w["dim"] == 3:
+        add_hbm_bytes(levels, per_level, args.steps)
     out = {
         "metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == B.MLMC_PREC_FP64 else
-                 "f64 Newton/residual/QoI + f32 CG (f64 CG on the 32^2 level)",
+                 "f64 nonlinear iteration/residual/QoI + f32 CG (f64 CG on the 32^2 level)",
         "data": "synthetic",
         "config": {"workload": w["name"], "N_l": w["N"], "grids": grids_of(w),
                    "steps_per_level": [w["m0"] * 2 ** l for l in range(w["levels"])],
@@ -376,27 +397,65 @@ def run_ours(args, w):
                    "layouts": ({str(l): ctx.layout(l) for l in range(w["levels"])}
                                if layouts else "automatic"),
                    "rmse_achieved": statistics.mean(rmse),
-                   "parallelism": "one thread-block cluster per sample; levels on concurrent streams"},
+                   "parallelism": ("one thread-block cluster per sample; levels on concurrent "
+                                   "streams" + ("" if world == 1 else
+                                                "; level ids sharded over %d ranks, one NCCL "
+                                                "all-gather + Chan merge per estimate" % world))},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * L,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        "roofline": roofline_3d(cg64_ni, cg_ni, nw_ni, solve_ms, dev_ms,
-                                                      nsolve / args.steps) if w["dim"] == 3 else
-                    {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     # measured with the automatic layouts only
-                     "traffic": TRAFFIC_2D_BYTES_PER_SOLVE_LAUNCH if all(
-                         ctx.layout(l) == 0 for l in range(w["levels"])) else None,
-                     "kernel": "solve_cluster_kernel (per-sample Newton-CG sweep), FP64 pipe",
-                     "peak_source": "FP64 FMA-chain probe on GB300 (measured)",
-                     "aggregate_tflops": aggregate, "aggregate_frac": aggregate / FP64_PEAK_TFLOPS,
-                     "solve_launches_per_step": nsolve / args.steps},
+        "gpu_launches": int(launches / args.steps) if launches else None,
+        "roofline": roofline_3d(levels, ms, peaks) if w["dim"] == 3 else
+                    roofline_2d(levels, ms, peaks, all(ctx.layout(l) == 0 for l in range(L))),
+        "levels": levels,
+        "peaks_measured": peaks,
         "clocks": clk,
         "cpu_baseline": cpu,
         "autotune": layouts or None,
     }
     out.update(extras)
     print(json.dumps(out))
+
+
+def level_bounds(per_level, steps, peaks):
+    """Each grid level's solve launches against their own bound: FP64 work
+    (nonlinear iterations, FP64 CG) over the measured FP64 FMA rate plus FP32
+    CG work over the FP32 rate gives the ALU-bound time; frac = that time /
+    the launches' measured time.  Per step (one estimate)."""
+    out = []
+    for l, v in enumerate(per_level):
+        ms = v["solve_ms"] / steps
+        f64 = (FLOP_NEWTON_NODE * v["newton_node_iters"] + FLOP_CG_NODE * v["cg64_node_iters"]) / steps
+        f32 = FLOP_CG_NODE * (v["cg_node_iters"] - v["cg64_node_iters"]) / steps
+        t_bound = f64 / (peaks["fp64_tflops"] * 1e12) + f32 / (peaks["fp32_tflops"] * 1e12)
+        out.append({"level": l, "solve_ms": ms, "launches": v["solve_launches"] / steps,
+                    "fp64_gflop": f64 * 1e-9, "fp32_gflop": f32 * 1e-9,
+                    "alu_bound_ms": t_bound * 1e3,
+                    "frac": t_bound * 1e3 / ms if ms > 0 else None,
+                    "retried_pseudo_steps_or_halvings": v["halvings"] / steps,
+                    "not_converged": v["not_converged"] / steps})
+    return out
+
+
+def roofline_2d(levels, step_ms, peaks, auto_layouts):
+    """The dominant kernel is the per-sample sweep; its bound is the ALU (FP64
+    for the nonlinear iterations and the FP64 CG, FP32 for the FP32 CG).
+    achieved = FP64-equivalent algorithmic flops (FP32 flops scaled by
+    peak64 / peak32) of the dominant grid level's launches over their
+    measured time; peak = the measured FP64 rate, so frac = ALU-bound time /
+    measured time of that level."""
+    dom = max(levels, key=lambda v: v["solve_ms"])
+    p64, p32 = peaks["fp64_tflops"], peaks["fp32_tflops"]
+    eq = (dom["fp64_gflop"] + dom["fp32_gflop"] * p64 / p32) * 1e9
+    achieved = eq / (dom["solve_ms"] * 1e-3) / 1e12 if dom["solve_ms"] > 0 else 0.0
+    tot_bound = sum(v["alu_bound_ms"] for v in levels)
+    return {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s",
+            "frac": achieved / p64,
+            # measured with the automatic layouts only, and on the earlier sweep
+            "traffic": None,
+            "kernel": "solve_cluster_kernel (per-sample sweep), grid level %d: FP64 + FP32 work "
+                      "as FP64-equivalent flops" % dom["level"],
+            "peak_source": "FP64 FMA-chain probe in this run (mlmc_probe_fma_rate), of measured",
+            "whole_estimate_frac": tot_bound / step_ms if step_ms > 0 else None}
 
 
 def measured_hbm_peak():
@@ -409,53 +468,95 @@ def measured_hbm_peak():
         return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
 
 
-def roofline_3d(cg64_ni, cg_ni, nw_ni, solve_ms, dev_ms, launches_per_step):
-    """HBM roofline of the global-memory sweep (3D levels): algorithmic bytes
-    from the node-weighted iteration counts over the solve launches' summed
-    CUDA-event time (launches overlap on concurrent streams) and over the
-    step's device time."""
+def roofline_3d(levels, step_ms, peaks):
+    """HBM roofline of the global-memory sweep (3D levels >= 1): algorithmic
+    bytes of the dominant grid level's launches (from its node-weighted
+    iteration counts) over their summed CUDA-event time (launches overlap on
+    concurrent streams), against the measured copy bandwidth."""
     peak, src = measured_hbm_peak()
-    nbytes = (BYTES_CG32_NODE_3D * (cg_ni - cg64_ni) + BYTES_CG64_NODE_3D * cg64_ni +
-              BYTES_NEWTON_NODE_3D * nw_ni)
-    achieved = nbytes / (solve_ms * 1e-3) / 1e9 if solve_ms > 0 else 0.0
-    aggregate = nbytes / (dev_ms * 1e-3) / 1e9 if dev_ms > 0 else 0.0
+    dom = max(levels, key=lambda v: v["solve_ms"])
+    achieved = dom["hbm_gb"] / (dom["solve_ms"] * 1e-3) if dom["solve_ms"] > 0 else 0.0
+    tot_gb = sum(v["hbm_gb"] for v in levels)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": "solve_cluster_kernel, global-memory layout (couplings streamed per pass)",
-            "peak_source": src, "aggregate_gbs": aggregate, "aggregate_frac": aggregate / peak,
-            "solve_launches_per_step": launches_per_step}
+            "kernel": "solve_cluster_kernel, global-memory layout (couplings streamed per pass), "
+                      "grid level %d" % dom["level"],
+            "peak_source": src, "aggregate_gbs": tot_gb / (step_ms * 1e-3) if step_ms > 0 else None,
+            "aggregate_frac": tot_gb / (step_ms * 1e-3) / peak if step_ms > 0 else None}
 
 
-def run_extras(w, B, prec, seed):
-    """Two measurements beside the step time, on the same workload.
+def add_hbm_bytes(levels, per_level, steps):
+    for v, c in zip(levels, per_level):
+        nb = (BYTES_CG32_NODE_3D * (c["cg_node_iters"] - c["cg64_node_iters"]) +
+              BYTES_CG64_NODE_3D * c["cg64_node_iters"] + BYTES_NEWTON_NODE_3D * c["newton_node_iters"])
+        v["hbm_gb"] = nb / steps * 1e-9
+        v["hbm_gbs"] = v["hbm_gb"] / (v["solve_ms"] * 1e-3) if v["solve_ms"] > 0 else None
+    return levels
 
-    time_to_eps: the adaptive driver (mlmc_run_to_rmse) from pilot counts to a
-    sampling error of eps / sqrt(2), eps = 1e-3 T; wall time of the call.  The
-    bias of this fixed 3-level hierarchy is reported; it exceeds eps, so only
-    the sampling part of the RMSE is driven to the target.  Beside it, the
-    plain FP64 form (block-per-sample kernel, one sample per launch) is
-    timed on a few pairs per level and its time for the same N_l is
-    extrapolated from those per-pair costs.
+
+def timed_run(ctx, N, seed, batch, stream):
+    """One estimate through mlmc_run, timed with CUDA events on `stream`."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = ctx.run(N, seed=seed, batch=batch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return res, e0.elapsed_time(e1) * 1e-3
+
+
+def run_extras(w, B, prec, seed, stream, peaks):
+    """Measurements beside the step time, on the same workload.
+
+    fp64_check: the same estimate (same seed and N_l) in FP64, its time and
+    the largest difference of its mean activation map from the timed
+    precision's, against the 0.1 eps the mixed form must stay within.
+
+    adaptive: the driver (mlmc_run_to_rmse) from pilot counts with eps = 1e-3 T;
+    it drives the sampling error to eps / sqrt(2) and reports whether the
+    bias estimate allows eps at all on this hierarchy (``reached``); only a
+    run that reached eps has a ``time_to_eps_s``.  Beside it, the plain FP64
+    one-sample-per-launch form's time for the same N_l, extrapolated from a
+    few timed pairs per level; the per-level diagnostics of the estimate; and
+    the same diagnostics with a fourth, finer level (256^2, 512 steps).
 
     serving: an open-loop Poisson stream of level-pair requests at 2000/s with
     per-request seeds and stimulus centres uniform in [0, 0.2]^2, the levels
     mixed in the proportions of the adaptive N_l, through the request server.
+
+    slab3d: one estimate of the 4-level 3D slab (N_l = 256/64/16/4) with the
+    HBM roofline of its global-memory sweep.
     """
     import numpy as np
     import torch
     from paper_1911_06066_gb300 import serving as S
+    from paper_1911_06066_gb300 import workloads as W
 
+    out = {}
     eps = 1e-3 * w["T"]
+    batch = max(w["N"])
+    # ---- the same estimate in FP64
     ctx = B.Context(B.make_config(w, prec, use_graph=True))
+    ctx64 = B.Context(B.make_config(w, B.MLMC_PREC_FP64, use_graph=True))
+    ctx64.run(w["N"], seed=seed, batch=batch)
+    r64, s64 = timed_run(ctx64, w["N"], seed, batch, stream)
+    rp, sp = timed_run(ctx, w["N"], seed, batch, stream)
+    dmean = float(np.abs(rp["mean"] - r64["mean"]).max())
+    out["fp64_check"] = {"fp64_seconds": s64, "timed_precision_seconds": sp,
+                         "max_abs_dmean": dmean, "tolerance": 0.1 * eps,
+                         "within": dmean <= 0.1 * eps,
+                         "workload": w["name"], "N_l": w["N"], "seed": seed}
+    del ctx64
+    # ---- adaptive driver, bias diagnostics
     ctx.run([64, 16, 4], seed=seed + 100, batch=64)          # warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = ctx.run_to_rmse(eps, [64, 16, 4], max_rounds=8, max_per_level=1 << 20, seed=seed + 200,
                           batch=512)
-    t_eps = time.perf_counter() - t0
+    t_run = time.perf_counter() - t0
     N = res["N_l"]
+    diag = ctx.diagnostics()
     stat = float(np.sqrt(np.sum(res["V_l"] / N)))
-    # the plain FP64 one-sample-per-launch form: per-pair cost on a few pairs
     plain = B.Context(B.make_config(w, B.MLMC_PREC_FP64, solver=B.MLMC_SOLVER_BLOCK))
     plain.run([1, 1, 1], seed=seed + 300, batch=1)
     per = []
@@ -468,15 +569,30 @@ def run_extras(w, B, prec, seed):
         plain.run_more([0] * w["levels"], cnt, seed=seed + 400, batch=1)
         per.append((time.perf_counter() - t1) / k)
     plain_s = float(np.sum(np.asarray(per) * N))
-    tte = {"eps": eps, "target_sampling_rmse": eps / math.sqrt(2.0), "seconds": t_eps,
-           "N_l": N.tolist(), "V_l": res["V_l"].tolist(), "C_l": res["C_l"].tolist(),
-           "sampling_rmse": stat, "bias": res["bias"], "rmse": res["rmse"],
-           "plain_fp64_one_sample_per_launch": {
-               "seconds_per_pair": per, "seconds_for_same_N_l": plain_s,
-               "how": "8/4/2 pairs per level timed, x N_l (extrapolated)"},
-           "speedup_vs_plain": plain_s / t_eps if t_eps > 0 else None}
-    del ctx, plain
-    # serving
+    out["adaptive"] = {
+        "eps": eps, "reached": bool(res["reached"]),
+        "time_to_eps_s": t_run if res["reached"] else None,
+        "seconds": t_run, "target_sampling_rmse": eps / math.sqrt(2.0), "sampling_rmse": stat,
+        "bias": res["bias"], "rmse": res["rmse"], "message": res["message"],
+        "N_l": N.tolist(), "V_l": res["V_l"].tolist(), "C_l": res["C_l"].tolist(),
+        "mean_correction_norm_l": diag["mean_norm"].tolist(), "weak_rate_alpha": diag["alpha"],
+        "censored_fraction_l": diag["censored"].tolist(),
+        "plain_fp64_one_sample_per_launch": {
+            "seconds_per_pair": per, "seconds_for_same_N_l": plain_s,
+            "how": "8/4/2 pairs per level timed, x N_l (extrapolated)"},
+        "same_N_l_ratio_plain_over_this": plain_s / t_run if t_run > 0 else None}
+    del plain
+    # a fourth, finer level (256^2, 512 steps) for the weak rate
+    w4 = dict(w, levels=4, N=[256, 64, 16, 8], name=w["name"] + "+256")
+    ctx4 = B.Context(B.make_config(w4, prec, use_graph=True))
+    r4, s4 = timed_run(ctx4, w4["N"], seed + 500, 256, stream)
+    d4 = ctx4.diagnostics()
+    out["bias_diagnostic_4_levels"] = {
+        "grids": grids_of(w4), "N_l": w4["N"], "seconds": s4,
+        "mean_correction_norm_l": d4["mean_norm"].tolist(), "weak_rate_alpha": d4["alpha"],
+        "censored_fraction_l": d4["censored"].tolist(), "V_l": r4["V_l"].tolist()}
+    del ctx4
+    # ---- serving
     mix = N / N.sum()
     srv_ctx = B.Context(B.make_config(w, prec))
     srv = B.Server(srv_ctx, max_batch=256, slots=6, mem_budget=8 << 30, max_wait_s=0.005)
@@ -503,7 +619,18 @@ def run_extras(w, B, prec, seed):
                                                    "throughput", "p50_ms", "p99_ms", "max_queue",
                                                    "batches", "failed")}
     serving["sustainable"].update({"rate": rate2, "requests": n2})
-    return {"time_to_eps": tte, "serving": serving}
+    out["serving"] = serving
+    del srv_ctx, ctx
+    # ---- the 4-level 3D slab
+    w3 = W.SLAB3D_4LVL
+    ctx3 = B.Context(B.make_config(w3, prec, use_graph=True))
+    ctx3.run([8, 4, 2, 1], seed=seed + 600, batch=8)         # warm: modules, graph shapes
+    r3, s3 = timed_run(ctx3, w3["N"], seed + 700, max(w3["N"]), stream)
+    lv3 = add_hbm_bytes(level_bounds(ctx3.level_stats(), 1, peaks), ctx3.level_stats(), 1)
+    out["slab3d"] = {"workload": w3["name"], "N_l": w3["N"], "grids": grids_of(w3),
+                     "seconds": s3, "rmse": r3["rmse"], "C_l": r3["C_l"].tolist(),
+                     "levels": lv3, "roofline": roofline_3d(lv3, s3 * 1e3, peaks)}
+    return out
 
 
 def run_profile_case(args, w):

@@ -51,7 +51,10 @@ typedef enum {
   MLMC_ERR_NOT_CONVERGED = -3,/* a sample's Newton iteration did not converge  */
   MLMC_ERR_TIMEOUT = -4,      /* a bounded device wait ran out                 */
   MLMC_ERR_CUDA = -5,         /* a CUDA runtime call failed                    */
-  MLMC_ERR_WORKSPACE = -6     /* workspace missing, too small or misaligned    */
+  MLMC_ERR_WORKSPACE = -6,    /* workspace missing, too small or misaligned    */
+  MLMC_WARN_BIAS = 1          /* mlmc_run_to_rmse: outputs valid and the sampling
+                                 error at its target, but the bias estimate exceeds
+                                 eps/sqrt(2), so the RMSE target is not reached    */
 } mlmc_status;
 
 typedef enum {
@@ -299,6 +302,16 @@ mlmc_status mlmc_set_layout(mlmc_ctx* ctx, int level, int layout);
 mlmc_status mlmc_run(mlmc_ctx* ctx, const int64_t* N_l, uint64_t seed, int batch, void* ws,
                      size_t ws_bytes, double* mean, double* var, double* V_l, double* C_l,
                      double* rmse, double* stats, void* stream);
+/* Per-level solve statistics (host out [n_levels][8]) of the solves on grid
+ * level l (as the fine member of pair l or the coarse member of pair l+1):
+ * out[8l + 0] the device ms of their solve-kernel launches in the last
+ * mlmc_run / mlmc_run_more / mlmc_run_to_rmse round (CUDA events around each
+ * launch, summed), [1] their number, and since the last reset: [2] CG iterations x
+ * nodes, [3] nonlinear iterations x nodes, [4] the part of [2] run in FP64,
+ * [5] CG truncations, [6] halvings or retried pseudo-steps, [7] solves that did
+ * not converge.  Used to set each level's work against its own bound. */
+mlmc_status mlmc_level_stats(mlmc_ctx* ctx, double* out);
+
 /* Workspace bytes for mlmc_run with the given counts (host N_l) and batch;
  * also for mlmc_run_more with N_l = its count. */
 mlmc_status mlmc_run_workspace_bytes(const mlmc_ctx* ctx, const int64_t* N_l, int batch,
@@ -319,7 +332,8 @@ mlmc_status mlmc_run_more(mlmc_ctx* ctx, const int64_t* first_id, const int64_t*
                           uint64_t seed, int batch, void* ws, size_t ws_bytes,
                           double* solve_seconds, void* stream);
 
-/* Adaptive MLMC with a fixed hierarchy (the sample allocation of Sec. 3):
+/* Adaptive MLMC with a fixed hierarchy (the sample allocation of Sec. 3.1.2,
+ * with the error of Eq. general-error-MLMC split into sampling error and bias):
  * runs the pilot counts N_pilot[l] (>= 1 each), then up to max_rounds times
  * estimates V_l (lumped-mass-weighted variance of Y_l) and the cost C_l per
  * pair (solve-kernel seconds, as for mlmc_run) and raises every level to
@@ -331,12 +345,29 @@ mlmc_status mlmc_run_more(mlmc_ctx* ctx, const int64_t* first_id, const int64_t*
  * [nodes_0] (may be NULL), V_l, C_l [n_levels] (may be NULL), rmse (as
  * mlmc_estimate, sampling error plus squared bias) and bias (the weighted norm
  * of the finest level's mean correction, an estimate of the discretisation
- * bias; 0 for one level) (may be NULL).  ws:
+ * bias; 0 for one level) (may be NULL).  The target RMSE <= eps also needs
+ * bias^2 <= eps^2 / 2: when the bias estimate is larger, the call returns
+ * MLMC_WARN_BIAS (outputs valid; mlmc_last_error says by how much) -- no
+ * sample count can reach eps on this hierarchy, only finer levels can.  ws:
  * mlmc_run_workspace_bytes(ctx, {batch, ..., batch}, batch) bytes. */
 mlmc_status mlmc_run_to_rmse(mlmc_ctx* ctx, double eps, const int64_t* N_pilot, int max_rounds,
                              int64_t max_per_level, uint64_t seed, int batch, void* ws,
                              size_t ws_bytes, int64_t* N_l, double* mean, double* var,
                              double* V_l, double* C_l, double* rmse, double* bias, void* stream);
+
+/* Row a11 diagnostics of the running estimates (host outputs, any may be NULL;
+ * synchronises the stream), for judging the bias of the hierarchy
+ * (Sec. 3.1.2, Eq. discretization-error and Eq. general-error-MLMC):
+ *   mean_norm [n_levels]: ||mean(Y_l)||_w, the level-0 lumped-mass-weighted L2
+ *     norm of each level's mean correction (of the level-0 mean for l = 0);
+ *   alpha: the fitted weak rate, the least-squares slope of
+ *     -log2 ||mean(Y_l)||_w over the correction levels l >= 1 (NaN with fewer
+ *     than two), so that the bias of level L is ~ ||mean(Y_L)|| 2^-alpha;
+ *   censored [n_levels]: the fraction of the injected level-l activation times
+ *     (every coarsest-grid node of every pair computed since the last reset)
+ *     equal to T, i.e. nodes the front had not reached by the end time. */
+mlmc_status mlmc_diagnostics(mlmc_ctx* ctx, double* mean_norm, double* alpha, double* censored,
+                             void* stream);
 
 /* Accumulator state (checkpoint / resume, and the cross-device merge).  The
  * state of a context is, per level l, the sample count N_l and per coarsest-
@@ -428,6 +459,15 @@ mlmc_status mlmc_server_estimate(mlmc_server* s, double* mean, double* var, doub
 const char* mlmc_server_error(mlmc_server* s);
 /* Stops admitting, waits for the batches in flight, frees everything. */
 void mlmc_server_destroy(mlmc_server* s);
+
+/* Measurement aid (the paper has no counterpart): the device's fused
+ * multiply-add rate in TFLOP/s (2 flop per FMA), FP64 (fp64 != 0) or FP32,
+ * from 8 independent FMA chains per thread on 16 x 256 threads per SM, timed
+ * with CUDA events on `stream` after a warm-up launch; synchronises it.  out:
+ * device scratch of >= 16 * 256 * 8 bytes per SM (written).  This is the ALU
+ * bound of the sweep's FP64 and FP32 work. */
+mlmc_status mlmc_probe_fma_rate(int fp64, void* out, size_t out_bytes, double* tflops,
+                                void* stream);
 
 /* Allocation-free variant of mlmc_solve (the paper has no counterpart; this is
  * a deployment aid).  For callers that may not allocate device memory -- for

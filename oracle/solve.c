@@ -21,11 +21,14 @@
  * convex implicit-Euler pseudo-steps); or_step_solve reaches the same point
  * faster by a gradient-flow continuation, and the tests pin the two together:
  *   - linearly implicit pseudo-steps (M/t + H(u)) d = -F(u), u += d, by
- *     Jacobi-preconditioned CG; t starts at 1/(2 max r'), doubles after every
- *     accepted step and is capped at FLOW_CAP / max_i (r'(u_i) - 1/dt), which
- *     keeps M/t + H positive definite (K is positive semidefinite).  Such a
- *     step never reverses the sign of the flow's unstable component near a
- *     saddle, so it does not jump between basins;
+ *     Jacobi-preconditioned CG; t starts at 1/(2 max r') and doubles after
+ *     every accepted step; a step whose CG meets non-positive curvature (M/t +
+ *     H not positive definite) is retried with t/4.  A step with M/t + H
+ *     positive definite never reverses the sign of the flow's unstable
+ *     component near a saddle (the linearised step multiplies it by
+ *     1/(1 - t lambda_u) > 0), so it does not jump between basins, and t can
+ *     grow as far as the local curvature allows -- near a nearly degenerate
+ *     saddle, where the flow crawls, that is what makes the continuation fast;
  *   - a step that would move some node by more than FLOW_MOVE is retried with
  *     a shorter t (counted as a halving);
  *   - once an accepted step moves no node by more than FLOW_NEWTON the flow has
@@ -43,7 +46,6 @@
 #include "oracle.h"
 
 /* Parameters of the gradient-flow continuation (see or_step_solve). */
-#define FLOW_CAP 0.5      /* pseudo-step t <= FLOW_CAP / max_i (r'(u_i) - 1/dt)   */
 #define FLOW_MOVE 0.3     /* largest nodal move of an accepted pseudo-step          */
 #define FLOW_TMIN 1e-9    /* pseudo-steps this short are accepted regardless        */
 #define FLOW_TMAX 1e20    /* upper bound of the growing pseudo-step                 */
@@ -170,26 +172,25 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
     int tr;
     if (flow) {
       /* linearly implicit pseudo-step of the gradient flow M v' = -F(v):
-         (M/t + H(u)) d = -F(u), t capped so that M/t + H stays positive
-         definite; once the flow has (nearly) arrived (an accepted move below
-         FLOW_NEWTON), Newton steps (t = infinity) finish the solve as long as
-         H is positive definite along their CG and they move no node by more
-         than 10 FLOW_NEWTON; a Newton step that fails either test is
-         discarded and the flow resumes with a tighter switch threshold */
-      double t = tau;
-      if (!newton_phase) {
-        double smax = -INFINITY;
-        for (int i = 0; i < n; ++i) {
-          double s = rxn_d(lv->c, lv->a, u[i]) - 1.0 / dt;
-          if (s > smax) smax = s;
-        }
-        if (smax > 0.0 && t > FLOW_CAP / smax) t = FLOW_CAP / smax;
-      }
+         (M/t + H(u)) d = -F(u), kept only if its CG met positive curvature
+         throughout (M/t + H positive definite); once the flow has (nearly)
+         arrived (an accepted move below FLOW_NEWTON), Newton steps
+         (t = infinity) finish the solve as long as their CG meets no
+         non-positive curvature and they move no node by more than
+         10 FLOW_NEWTON; a Newton step that fails either test is discarded and
+         the flow resumes with a tighter switch threshold */
+      const double t = tau;
       int cg = shifted_cg(n, mass, Kst, lv, u, newton_phase ? 0.0 : 1.0 / t, F, d, &tr);
       if (cg < 0) break;
       cg_total += cg; trunc_total += tr;
       double dmax = 0.0;
       for (int i = 0; i < n; ++i) if (fabs(d[i]) > dmax) dmax = fabs(d[i]);
+      if (!newton_phase && tr && t > FLOW_TMIN) {
+        /* M/t + H is not positive definite: retry with a quarter of t */
+        tau = 0.25 * t;
+        ++halvings;
+        continue;
+      }
       if (newton_phase) {
         if (tr || dmax > 10.0 * sw) {
           newton_phase = 0;

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libmlmc_gb300.so")
 
 MLMC_MAX_LEVELS = 8
 MLMC_OK = 0
+MLMC_WARN_BIAS = 1
 MLMC_PREC_FP64 = 0
 MLMC_PREC_MIXED = 1
 STATUS = {0: "MLMC_OK", -1: "MLMC_ERR_ARG", -2: "MLMC_ERR_OOM", -3: "MLMC_ERR_NOT_CONVERGED",
@@ -103,6 +104,8 @@ def lib():
             "mlmc_run_more": ([vp, vp, vp, u64, ip, vp, sz, vp, vp], ip),
             "mlmc_run_to_rmse": ([vp, C.c_double, vp, ip, i64, u64, ip, vp, sz, vp, vp, vp, vp, vp,
                                   vp, vp, vp], ip),
+            "mlmc_diagnostics": ([vp, vp, vp, vp, vp], ip),
+            "mlmc_level_stats": ([vp, vp], ip),
             "mlmc_get_state": ([vp, vp, vp, vp, vp, vp], ip),
             "mlmc_set_state": ([vp, vp, vp, vp, vp, vp], ip),
             "mlmc_merge_states": ([ip, i64, vp, vp, vp, vp, vp, vp, vp, vp], ip),
@@ -119,6 +122,7 @@ def lib():
             "mlmc_server_error": ([vp], C.c_char_p),
             "mlmc_server_destroy": ([vp], None),
             "mlmc_solve_noalloc": ([C.POINTER(mlmc_config), ip, vp, ip, vp, vp, vp], ip),
+            "mlmc_probe_fma_rate": ([ip, vp, sz, C.POINTER(C.c_double), vp], ip),
         }
         for name, (args, res) in sig.items():
             f = getattr(l, name)
@@ -136,11 +140,24 @@ def exported_symbols():
             "mlmc_slab_residual",
             "mlmc_activation", "mlmc_sample_level", "mlmc_accumulate", "mlmc_reset",
             "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_run_more",
-            "mlmc_run_to_rmse", "mlmc_get_state", "mlmc_set_state", "mlmc_merge_states",
+            "mlmc_run_to_rmse", "mlmc_diagnostics", "mlmc_level_stats", "mlmc_get_state", "mlmc_set_state", "mlmc_merge_states",
             "mlmc_autotune", "mlmc_get_layout", "mlmc_set_layout", "mlmc_server_create",
             "mlmc_server_submit", "mlmc_server_poll", "mlmc_server_drain", "mlmc_server_stats",
             "mlmc_server_clock", "mlmc_server_estimate", "mlmc_server_error",
-            "mlmc_server_destroy", "mlmc_solve_noalloc"]
+            "mlmc_server_destroy", "mlmc_solve_noalloc", "mlmc_probe_fma_rate"]
+
+
+def fma_rate(fp64=True, stream=None):
+    """Measured FMA rate of the current device in TFLOP/s (mlmc_probe_fma_rate)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = torch.empty(16 * 256 * 8 * sms, dtype=torch.uint8, device="cuda")
+    r = C.c_double()
+    st = lib().mlmc_probe_fma_rate(1 if fp64 else 0, C.c_void_p(out.data_ptr()), out.numel(),
+                                   C.byref(r), _stream(stream))
+    if st != MLMC_OK:
+        raise MLMCError(st, lib().mlmc_last_error(None).decode())
+    return r.value
 
 
 def _dp(a):
@@ -426,7 +443,9 @@ class Context:
 
     def run_to_rmse(self, eps, N_pilot, max_rounds=8, max_per_level=1 << 20, seed=0, batch=64,
                     stream=None):
-        """Adaptive MLMC to sampling error eps / sqrt(2) (mlmc_run_to_rmse)."""
+        """Adaptive MLMC to sampling error eps / sqrt(2) (mlmc_run_to_rmse).
+        ``reached`` is False when the bias estimate exceeds eps / sqrt(2)
+        (MLMC_WARN_BIAS: the RMSE target is out of reach of this hierarchy)."""
         L = self.cfg.n_levels
         n0, _, _ = self.level_info(0)
         P = np.ascontiguousarray(N_pilot, np.int64)
@@ -435,11 +454,33 @@ class Context:
         rmse, bias = C.c_double(), C.c_double()
         nb = self.run_workspace_bytes(np.full(L, batch, np.int64), batch)
         ws = self.workspace(nb, key="run")
-        self._check(lib().mlmc_run_to_rmse(self.h, eps, _dp(P), max_rounds, max_per_level, seed,
-                                           batch, _p(ws), ws.numel(), _dp(N), _dp(mean), _dp(var),
-                                           _dp(V), _dp(Cl), C.byref(rmse), C.byref(bias),
+        st = lib().mlmc_run_to_rmse(self.h, eps, _dp(P), max_rounds, max_per_level, seed, batch,
+                                    _p(ws), ws.numel(), _dp(N), _dp(mean), _dp(var), _dp(V),
+                                    _dp(Cl), C.byref(rmse), C.byref(bias), _stream(stream))
+        if st != MLMC_WARN_BIAS:
+            self._check(st)
+        return dict(N_l=N, mean=mean, var=var, V_l=V, C_l=Cl, rmse=rmse.value, bias=bias.value,
+                    reached=st == MLMC_OK,
+                    message=lib().mlmc_last_error(self.h).decode() if st != MLMC_OK else "")
+
+    def level_stats(self):
+        """Per-level solve statistics (mlmc_level_stats): a list of dicts."""
+        L = self.cfg.n_levels
+        out = np.zeros(8 * L)
+        self._check(lib().mlmc_level_stats(self.h, _dp(out)))
+        keys = ("solve_ms", "solve_launches", "cg_node_iters", "newton_node_iters",
+                "cg64_node_iters", "truncations", "halvings", "not_converged")
+        return [dict(zip(keys, out[8 * l:8 * l + 8].tolist())) for l in range(L)]
+
+    def diagnostics(self, stream=None):
+        """Per-level ||mean(Y_l)||_w, the fitted weak rate alpha and the censored
+        fractions of the running estimates (mlmc_diagnostics)."""
+        L = self.cfg.n_levels
+        nrm, cens = np.zeros(L), np.zeros(L)
+        alpha = C.c_double()
+        self._check(lib().mlmc_diagnostics(self.h, _dp(nrm), C.byref(alpha), _dp(cens),
                                            _stream(stream)))
-        return dict(N_l=N, mean=mean, var=var, V_l=V, C_l=Cl, rmse=rmse.value, bias=bias.value)
+        return dict(mean_norm=nrm, alpha=alpha.value, censored=cens)
 
     def autotune(self, level, n, seed=0, first_id=0, stream=None):
         """Times every feasible solve layout of ``level`` on n samples and keeps

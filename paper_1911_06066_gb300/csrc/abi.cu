@@ -370,7 +370,7 @@ extern "C" mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* 
   if (!check_ws(ctx, ws, ws_bytes, kl_tc_workspace_bytes(ctx->M, n))) return MLMC_ERR_WORKSPACE;
   CK(ctx, launch_kl_field_tc(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_idx,
                              ctx->d_phi32[level][0], ctx->d_phi32[level][1],
-                             ctx->d_phi32[level][2], xi, n, Z, ws, ctx->d_cnt + 6,
+                             ctx->d_phi32[level][2], xi, n, Z, ws, ctx->d_cnt + CNT_TC_TIMEOUT,
                              (cudaStream_t)stream));
   ctx->launches += 2;
   return MLMC_OK;
@@ -440,6 +440,7 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     e0 = ctx->ev_pool[ctx->ev_used++];
     e1 = ctx->ev_pool[ctx->ev_used++];
     ctx->ev_level.push_back(ctx->prof_level);
+    ctx->ev_grid.push_back(level);
     CK(ctx, cudaEventRecordWithFlags(e0, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
   const SolverParams sp = level_solver_params(ctx->cfg, lv, mixed);
@@ -453,12 +454,13 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     level_gmg(ctx->cfg, lv, &mg);
     g.mg = mg.G > 0 ? (void*)(ws + w.mg) : nullptr;
     CK(ctx, launch_solve_cluster(lv, ph, sp, mixed, plan, n, coef64, coef32, slab, t_act, info,
-                                 ctx->d_cnt, g, mg, st));
+                                 ctx->d_cnt + CNT_LEVEL + CNT_PER_LEVEL * level, g, mg, st));
   }
   else
     CK(ctx, launch_solve(lv, ph, sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
                          (double*)(ws + w.F), (double*)(ws + w.Ku), (double*)(ws + w.Kd),
-                         (void*)(ws + w.kr), t_act, info, ctx->d_cnt, st));
+                         (void*)(ws + w.kr), t_act, info,
+                         ctx->d_cnt + CNT_LEVEL + CNT_PER_LEVEL * level, st));
   if (ctx->prof)
     CK(ctx, cudaEventRecordWithFlags(e1, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   ctx->launches += 2;
@@ -625,7 +627,7 @@ mlmc_status mlmc::sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, con
     return r;
   if (level > 0 && (r = order_after(ctx, st_c, st_f)) != MLMC_OK) return r;
   CK(ctx, launch_pair_diff(ctx->lv[0], ctx->lv[level], level > 0 ? &ctx->lv[level - 1] : nullptr, tf,
-                           tc, n, y, y2, st_f));
+                           tc, n, y, y2, ctx->d_cnt + CNT_CENSORED + level, st_f));
   ctx->launches += 1;
   return MLMC_OK;
 }
@@ -843,6 +845,9 @@ static mlmc_status enqueue_levels(mlmc_ctx* ctx, const int64_t* first_id, const 
 static mlmc_status fill_stats(mlmc_ctx* ctx, double* stats) {
   unsigned long long cnt[N_COUNTERS];
   CK(ctx, cudaMemcpy(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
+  unsigned long long tot[6] = {0, 0, 0, 0, 0, 0};
+  for (int l = 0; l < MLMC_MAX_LEVELS; ++l)
+    for (int q = 0; q < 6; ++q) tot[q] += cnt[CNT_LEVEL + CNT_PER_LEVEL * l + q];
   if (stats) {
     double solve_ms = 0.0;
     for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
@@ -852,23 +857,52 @@ static mlmc_status fill_stats(mlmc_ctx* ctx, double* stats) {
     }
     stats[0] = solve_ms;
     stats[1] = (double)(ctx->ev_used / 2);
-    stats[2] = (double)cnt[1];
-    stats[3] = (double)cnt[2];
-    stats[4] = (double)cnt[3];
-    stats[5] = (double)cnt[4];
-    stats[6] = (double)cnt[0];
+    stats[2] = (double)tot[1];
+    stats[3] = (double)tot[2];
+    stats[4] = (double)tot[3];
+    stats[5] = (double)tot[4];
+    stats[6] = (double)tot[0];
     stats[7] = (double)ctx->launches;
-    stats[8] = (double)cnt[5];
+    stats[8] = (double)tot[5];
   }
-  if (cnt[6]) {
+  if (cnt[CNT_TC_TIMEOUT]) {
     char b[96];
-    snprintf(b, sizeof b, "%llu KL tensor-core tiles timed out waiting for their MMAs", cnt[6]);
+    snprintf(b, sizeof b, "%llu KL tensor-core tiles timed out waiting for their MMAs", cnt[CNT_TC_TIMEOUT]);
     return fail(ctx, MLMC_ERR_TIMEOUT, b);
   }
-  if (cnt[0]) {
+  if (tot[0]) {
     char b[96];
-    snprintf(b, sizeof b, "%llu sample solves did not converge", cnt[0]);
+    snprintf(b, sizeof b, "%llu sample solves did not converge", tot[0]);
     return fail(ctx, MLMC_ERR_NOT_CONVERGED, b);
+  }
+  return MLMC_OK;
+}
+
+// Per-level counters of the solves since the last reset and the solve-kernel
+// device time of the last run call's launches of each level.
+extern "C" mlmc_status mlmc_level_stats(mlmc_ctx* ctx, double* out) {
+  if (!ctx || !out) return MLMC_ERR_ARG;
+  unsigned long long cnt[N_COUNTERS];
+  CK(ctx, cudaMemcpy(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
+  const int L = ctx->cfg.n_levels;
+  for (int l = 0; l < L; ++l) {
+    double* o = out + 8 * l;
+    o[0] = 0.0;
+    o[1] = 0.0;
+    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+      if (ctx->ev_grid[i / 2] != l) continue;
+      float ms = 0.f;
+      CK(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+      o[0] += ms;
+      o[1] += 1.0;
+    }
+    const unsigned long long* c = cnt + CNT_LEVEL + CNT_PER_LEVEL * l;
+    o[2] = (double)c[1];   // CG iterations x nodes
+    o[3] = (double)c[2];   // nonlinear iterations x nodes
+    o[4] = (double)c[5];   // CG iterations x nodes in FP64
+    o[5] = (double)c[3];   // truncations
+    o[6] = (double)c[4];   // halvings / retried pseudo-steps
+    o[7] = (double)c[0];   // non-converged solves
   }
   return MLMC_OK;
 }
@@ -878,6 +912,7 @@ static mlmc_status run_begin(mlmc_ctx* ctx, void* stream) {
   if (r != MLMC_OK) return r;
   ctx->ev_used = 0;
   ctx->ev_level.clear();
+  ctx->ev_grid.clear();
   ctx->sync_used = 0;
   ctx->launches = 0;
   return MLMC_OK;
@@ -916,6 +951,7 @@ extern "C" mlmc_status mlmc_run_more(mlmc_ctx* ctx, const int64_t* first_id, con
   if (!check_ws(ctx, ws, ws_bytes, run_ws(ctx, count, batch))) return MLMC_ERR_WORKSPACE;
   ctx->ev_used = 0;
   ctx->ev_level.clear();
+  ctx->ev_grid.clear();
   ctx->sync_used = 0;
   double lvl_ms[MLMC_MAX_LEVELS];
   mlmc_status r = run_levels(ctx, first_id, count, seed, batch, (char*)ws, (cudaStream_t)stream, lvl_ms);
@@ -953,6 +989,7 @@ extern "C" mlmc_status mlmc_run_to_rmse(mlmc_ctx* ctx, double eps, const int64_t
   for (int round = 0;; ++round) {
     ctx->ev_used = 0;
     ctx->ev_level.clear();
+    ctx->ev_grid.clear();
     ctx->sync_used = 0;
     if ((r = run_levels(ctx, first, cnt, seed, batch, (char*)ws, st, lvl_ms)) != MLMC_OK) return r;
     for (int l = 0; l < L; ++l) {
@@ -978,10 +1015,66 @@ extern "C" mlmc_status mlmc_run_to_rmse(mlmc_ctx* ctx, double eps, const int64_t
     }
     if (more == 0) break;
   }
-  if ((r = estimate_impl(ctx, mean, var, nullptr, nullptr, V_l, nullptr, rmse, bias, stream)) != MLMC_OK)
+  double b = 0.0;
+  if ((r = estimate_impl(ctx, mean, var, nullptr, nullptr, V_l, nullptr, rmse, &b, stream)) != MLMC_OK)
     return r;
+  if (bias) *bias = b;
   if (C_l)
     for (int l = 0; l < L; ++l) C_l[l] = Cl[l];
+  // The allocation drives the sampling error to eps^2 / 2; the target
+  // sum_l V_l / N_l + bias^2 <= eps^2 also needs bias^2 <= eps^2 / 2, which no
+  // sample count changes on a fixed hierarchy.
+  if (b * b > 0.5 * eps * eps) {
+    char m[200];
+    snprintf(m, sizeof m, "mlmc_run_to_rmse: sampling error at target, but the bias estimate %.4g "
+             "exceeds eps/sqrt(2) = %.4g: eps is not reached with %d levels", b, eps / sqrt(2.0), L);
+    ctx->err = m;
+    return MLMC_WARN_BIAS;
+  }
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_diagnostics(mlmc_ctx* ctx, double* mean_norm, double* alpha,
+                                        double* censored, void* stream) {
+  if (!ctx) return MLMC_ERR_ARG;
+  const int L = ctx->cfg.n_levels;
+  const int64_t n0 = ctx->lv[0].nodes;
+  std::vector<double> mean_l((size_t)L * n0);
+  mlmc_status r = estimate_impl(ctx, nullptr, nullptr, mean_l.data(), nullptr, nullptr, nullptr,
+                                nullptr, nullptr, stream);
+  if (r != MLMC_OK) return r;
+  unsigned long long cnt[N_COUNTERS];
+  CK(ctx, cudaMemcpy(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost));
+  // level-0 lumped mass: cell volume times 1/2 per axis on which the node is
+  // on the boundary
+  const LevelDesc& l0 = ctx->lv[0];
+  std::vector<double> nrm(L, 0.0);
+  for (int64_t A = 0; A < n0; ++A) {
+    const int64_t i = A % l0.N[0], j = (A / l0.N[0]) % l0.N[1], k = A / ((int64_t)l0.N[0] * l0.N[1]);
+    double w = l0.vol;
+    if (i == 0 || i == l0.n[0]) w *= 0.5;
+    if (j == 0 || j == l0.n[1]) w *= 0.5;
+    if (l0.dim == 3 && (k == 0 || k == l0.n[2])) w *= 0.5;
+    for (int l = 0; l < L; ++l) nrm[l] += w * mean_l[(size_t)l * n0 + A] * mean_l[(size_t)l * n0 + A];
+  }
+  for (int l = 0; l < L; ++l) {
+    nrm[l] = sqrt(nrm[l]);
+    if (mean_norm) mean_norm[l] = nrm[l];
+    if (censored)
+      censored[l] = ctx->N_acc[l] > 0 ? (double)cnt[CNT_CENSORED + l] / ((double)ctx->N_acc[l] * (double)n0)
+                                      : 0.0;
+  }
+  if (alpha) {
+    // least-squares slope of -log2 ||mean(Y_l)|| over the correction levels l >= 1
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    int m = 0;
+    for (int l = 1; l < L; ++l) {
+      if (!(nrm[l] > 0.0)) continue;
+      const double y = -log2(nrm[l]);
+      sx += l; sy += y; sxx += (double)l * l; sxy += l * y; ++m;
+    }
+    *alpha = m >= 2 ? (m * sxy - sx * sy) / (m * sxx - sx * sx) : NAN;
+  }
   return MLMC_OK;
 }
 

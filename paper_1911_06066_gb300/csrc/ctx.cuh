@@ -33,6 +33,7 @@ struct mlmc_ctx {
   long launches = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_level;    // level pair of each (start, end) event pair
+  std::vector<int> ev_grid;     // grid level of the solve it brackets
   int prof_level = 0;
   size_t ev_used = 0;
   // per-level solver layout chosen by mlmc_autotune: 0 = the smallest

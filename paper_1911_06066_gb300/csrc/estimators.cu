@@ -36,27 +36,38 @@ __device__ inline int64_t injected_node(const LevelDesc& l0, const LevelDesc& lf
   return ((int64_t)(k * r) * lf.N[1] + (int64_t)j * r) * lf.N[0] + (int64_t)i * r;
 }
 
+// cens (device, may be NULL): count of injected fine activation times equal to
+// T (never activated by the end time), warp-aggregated.
 __global__ void pair_diff_kernel(LevelDesc l0, LevelDesc lf, LevelDesc lc, bool has_coarse,
                                  const double* __restrict__ tf, const double* __restrict__ tc,
-                                 int n, double* __restrict__ y, double* __restrict__ y2) {
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (int64_t)n * l0.nodes) return;
-  int s = (int)(g / l0.nodes);
-  int64_t A0 = g % l0.nodes;
-  double a = tf[(int64_t)s * lf.nodes + injected_node(l0, lf, A0)];
-  double b = has_coarse ? tc[(int64_t)s * lc.nodes + injected_node(l0, lc, A0)] : 0.0;
-  y[g] = a - b;
-  y2[g] = a * a - b * b;
+                                 int n, double* __restrict__ y, double* __restrict__ y2,
+                                 unsigned long long* cens) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = g < (int64_t)n * l0.nodes;
+  bool censored = false;
+  if (valid) {
+    const int s = (int)(g / l0.nodes);
+    const int64_t A0 = g % l0.nodes;
+    const double a = tf[(int64_t)s * lf.nodes + injected_node(l0, lf, A0)];
+    const double b = has_coarse ? tc[(int64_t)s * lc.nodes + injected_node(l0, lc, A0)] : 0.0;
+    y[g] = a - b;
+    y2[g] = a * a - b * b;
+    censored = a >= lf.T;
+  }
+  if (cens) {
+    const unsigned m = __ballot_sync(0xffffffffu, censored);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(cens, (unsigned long long)__popc(m));
+  }
 }
 
 cudaError_t launch_pair_diff(const LevelDesc& l0, const LevelDesc& lf, const LevelDesc* lc,
                              const double* tf, const double* tc, int n, double* y, double* y2,
-                             cudaStream_t st) {
+                             unsigned long long* cens, cudaStream_t st) {
   int64_t total = (int64_t)n * l0.nodes;
   if (total == 0) return cudaSuccess;
   int bs = 256;
   pair_diff_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(
-      l0, lf, lc ? *lc : l0, lc != nullptr, tf, tc, n, y, y2);
+      l0, lf, lc ? *lc : l0, lc != nullptr, tf, tc, n, y, y2, cens);
   return cudaGetLastError();
 }
 

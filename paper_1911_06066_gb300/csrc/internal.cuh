@@ -51,16 +51,15 @@ struct SolverParams {
 // c((1+a)^2/3 - a)).  Such a step has several roots; the root is the end
 // point of the gradient flow M v' = -F(v) of the step energy from u_{k-1},
 // the local minimum in whose basin u_{k-1} lies.  It is reached by linearly
-// implicit pseudo-steps (M/t + H(u)) d = -F(u): t starts at tau0, doubles
-// after each accepted step and is capped at FLOW_CAP / max_i (r'(u_i) - 1/dt),
-// which keeps M/t + H positive definite, so that a step never reverses the
-// flow's unstable component near a saddle; a step moving a node by more than
-// FLOW_MOVE is retried shorter; once an accepted step moves no node by more
-// than the switch threshold (FLOW_NEWTON at first) Newton steps finish the
-// solve while their CG meets only positive curvature and they move no node by
-// more than 10x the threshold (else the flow resumes with a 10x smaller
-// threshold).
-constexpr double FLOW_CAP = 0.5;
+// implicit pseudo-steps (M/t + H(u)) d = -F(u): t starts at tau0 and doubles
+// after each accepted step; a step whose CG meets non-positive curvature (M/t
+// + H not positive definite) is retried with t/4 -- with M/t + H positive
+// definite a step never reverses the flow's unstable component near a saddle
+// -- and a step moving a node by more than FLOW_MOVE is retried shorter; once
+// an accepted step moves no node by more than the switch threshold
+// (FLOW_NEWTON at first) Newton steps finish the solve while their CG meets
+// only positive curvature and they move no node by more than 10x the
+// threshold (else the flow resumes with a 10x smaller threshold).
 constexpr double FLOW_MOVE = 0.3;
 constexpr double FLOW_TMIN = 1e-9;
 constexpr double FLOW_TMAX = 1e20;
@@ -202,19 +201,28 @@ cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const S
                                  const float* coef32, double* slab, double* t_act,
                                  mlmc_sample_info* info, unsigned long long* counters,
                                  const ClusterGlobal& g, const MGDesc& mg, cudaStream_t st);
-// counters (device, may be NULL): [0] non-converged solves, [1] CG iterations x
-// nodes, [2] Newton iterations x nodes, [3] CG truncations, [4] halvings,
-// [5] CG iterations x nodes run in FP64 (the others run in FP32), [6] tensor-
-// core KL tiles whose bounded wait ran out.
-constexpr int N_COUNTERS = 7;
+// counters (device, may be NULL) of one solve launch: [0] non-converged
+// solves, [1] CG iterations x nodes, [2] nonlinear iterations x nodes, [3] CG
+// truncations, [4] halvings / retried pseudo-steps, [5] CG iterations x nodes
+// run in FP64 (the others run in FP32).  A context keeps one such block of
+// CNT_PER_LEVEL counters per level at CNT_LEVEL + CNT_PER_LEVEL l, after its
+// global counters: [6] tensor-core KL tiles whose bounded wait ran out,
+// [7 + l] injected level-l activation times equal to T (censored).
+constexpr int CNT_TC_TIMEOUT = 6;
+constexpr int CNT_CENSORED = 7;
+constexpr int CNT_LEVEL = CNT_CENSORED + MLMC_MAX_LEVELS;
+constexpr int CNT_PER_LEVEL = 8;
+constexpr int N_COUNTERS = CNT_LEVEL + CNT_PER_LEVEL * MLMC_MAX_LEVELS;
 cudaError_t launch_slab_residual(const LevelDesc& lv, const Physics& ph, const double* coef64,
                                  const double* slab, int n, double* F, double* res_max,
                                  cudaStream_t st);
 cudaError_t launch_activation(const LevelDesc& lv, const double* slab, int n, double* t_act,
                               cudaStream_t st);
+// cens (device, may be NULL): incremented by the number of injected fine
+// activation times equal to T (censored).
 cudaError_t launch_pair_diff(const LevelDesc& l0, const LevelDesc& lf, const LevelDesc* lc,
                              const double* tf, const double* tc, int n, double* y, double* y2,
-                             cudaStream_t st);
+                             unsigned long long* cens, cudaStream_t st);
 cudaError_t launch_accumulate(int64_t nodes0, const double* y, const double* y2, int n,
                               int64_t n_old, double* mean, double* m2, double* mean2,
                               cudaStream_t st);

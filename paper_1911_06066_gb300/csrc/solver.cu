@@ -14,9 +14,9 @@
 // M v' = -F_k(v) from u_{k-1}: the minimum in whose basin u_{k-1} lies.
 //   * Levels with several roots (sp.flow): gradient-flow continuation by
 //     linearly implicit pseudo-steps (M/t + H(u)) d = -F(u), u += d, with the
-//     pseudo-step t growing x2 per accepted step from 1/(2 max r'), capped at
-//     FLOW_CAP / max_i (r'(u_i) - 1/dt) so that M/t + H stays positive
-//     definite, retried shorter when it would move a node by more than
+//     pseudo-step t growing x2 per accepted step from 1/(2 max r'), retried
+//     with t/4 when the CG meets non-positive curvature (M/t + H must stay
+//     positive definite) and shorter when it would move a node by more than
 //     FLOW_MOVE, and finished by Newton steps (t = infinity) once the flow
 //     has nearly arrived (see SolverParams in internal.cuh).
 //   * Other levels: H is positive definite for every state and the root
@@ -149,23 +149,14 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
   for (int step = 1; step <= lv.m; ++step) {
     const double* up = sl ? sl + (int64_t)(step - 1) * N : ub + (int64_t)((step - 1) & 1) * N;
     double* u = sl ? sl + (int64_t)step * N : ub + (int64_t)(step & 1) * N;
-    double smax = 0.0;   // max_i (r'(u_i) - 1/dt), clipped at 0 (continuation levels)
-    {
-      double s_loc = 0.0;
-      for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {
-        const double ua = up[A];
-        u[A] = ua;
-        s_loc = fmax(s_loc, rxn_d(ph, ua) - inv_dt);
-      }
-      smax = block_max(s_loc, sh);   // also publishes u
-    }
+    for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) u[A] = up[A];
+    __syncthreads();
     double tau = sp.tau0, sw = FLOW_NEWTON;
     bool newton_phase = false;
     bool conv = false, lin_fail = false;
     int it;
     for (it = 1; it <= sp.newton_max; ++it) {
-      double t = tau;
-      if (sp.flow && !newton_phase && smax > 0.0 && t > FLOW_CAP / smax) t = FLOW_CAP / smax;
+      const double t = tau;
       const double shift = sp.flow && !newton_phase ? 1.0 / t : 0.0;
       // residual, Hessian diagonal, CG start (r = -F, z = P^-1 r, p = z, d = 0).
       // FP32 CG on grids with a tiny lumped mass per time step (sp.cg_scale):
@@ -261,18 +252,17 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
         if (newton_phase) {
           accept = !(truncated || dmax > 10.0 * sw);
           if (!accept) { newton_phase = false; sw *= 0.1; ++halvings; }
+        } else if (truncated && t > FLOW_TMIN) {
+          accept = false;              // M/t + H not positive definite
+          tau = 0.25 * t;
+          ++halvings;
         } else {
           accept = !(dmax > FLOW_MOVE && t > FLOW_TMIN);
           if (!accept) { tau = t * 0.5 * FLOW_MOVE / dmax; ++halvings; }
         }
         if (!accept) continue;       // the state is unchanged; retry
-        double s_loc = 0.0;
-        for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {
-          const double un = u[A] + (double)d[A];
-          u[A] = un;
-          s_loc = fmax(s_loc, rxn_d(ph, un) - inv_dt);
-        }
-        smax = block_max(s_loc, sh);
+        for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) u[A] += (double)d[A];
+        __syncthreads();
         if (dmax <= sp.newton_tol) { conv = true; break; }
         if (!newton_phase) {
           if (dmax <= sw) newton_phase = true;

@@ -362,25 +362,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     double* u = (step & 1) ? ubuf1 : ubuf0;
     const double* up = (step & 1) ? ubuf0 : ubuf1;
     const View<double>& uv = (step & 1) ? uv1 : uv0;
+    for (int a = tid; a < b.nb; a += NT) u[a] = up[a];
+    cluster_barrier(cl, b.C);
     // On levels whose steps have several roots (sp.flow) the step follows the
-    // gradient-flow continuation (see SolverParams): smax = max_i (r'(u_i) -
-    // 1/dt), clipped at 0, of the current state caps the pseudo-step.
-    double smax = 0.0;
-    {
-      double s_loc = 0.0;
-      for (int a = tid; a < b.nb; a += NT) {
-        const double ua = up[a];
-        u[a] = ua;
-        if (sp.flow) s_loc = fmax(s_loc, rxn_d(ph, ua) - inv_dt);
-      }
-      if (sp.flow) {
-        double v1[1] = {s_loc};
-        cluster_reduce<NT, double, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
-        smax = bc[0];
-      } else {
-        cluster_barrier(cl, b.C);
-      }
-    }
+    // gradient-flow continuation (see SolverParams).
     double tau = sp.tau0, sw = FLOW_NEWTON;
     bool newton_phase = false;
     bool conv = false, lin_fail = false;
@@ -388,8 +373,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     for (it = 1; it <= sp.newton_max; ++it) {
       // pseudo-step of the continuation (shift = M/t on the Hessian diagonal),
       // or a Newton step (shift 0)
-      double t = tau;
-      if (sp.flow && !newton_phase && smax > 0.0 && t > FLOW_CAP / smax) t = FLOW_CAP / smax;
+      const double t = tau;
       const double shift = sp.flow && !newton_phase ? 1.0 / t : 0.0;
       // residual, Hessian diagonal and the CG start r = -F, z = P^-1 r, p = z, d = 0
       // FP32 CG on grids with a tiny lumped mass per time step (sp.cg_scale,
@@ -564,22 +548,17 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         if (newton_phase) {
           accept = !(truncated || dmax > 10.0 * sw);
           if (!accept) { newton_phase = false; sw *= 0.1; ++halvings; }
+        } else if (truncated && t > FLOW_TMIN) {
+          accept = false;              // M/t + H not positive definite
+          tau = 0.25 * t;
+          ++halvings;
         } else {
           accept = !(dmax > FLOW_MOVE && t > FLOW_TMIN);
           if (!accept) { tau = t * 0.5 * FLOW_MOVE / dmax; ++halvings; }
         }
         if (!accept) continue;       // the state is unchanged; retry
-        double s_loc = 0.0;
-        for (int a = tid; a < b.nb; a += NT) {
-          const double un = u[a] + (double)d[a];
-          u[a] = un;
-          s_loc = fmax(s_loc, rxn_d(ph, un) - inv_dt);
-        }
-        {
-          double v1[1] = {s_loc};
-          cluster_reduce<NT, double, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
-          smax = bc[0];
-        }
+        for (int a = tid; a < b.nb; a += NT) u[a] += (double)d[a];
+        cluster_barrier(cl, b.C);
         if (dmax <= sp.newton_tol) { conv = true; break; }
         if (!newton_phase) {
           if (dmax <= sw) newton_phase = true;

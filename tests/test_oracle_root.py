@@ -54,7 +54,7 @@ def _multi_root(w, level):
 @pytest.mark.parametrize("name,level,samples,steps", [
     ("2d", 0, 16, 64),      # 32^2, 64 steps (all): c dt max r' = 2.37
     ("2d", 1, 16, 16),      # 64^2, first 16 of 128 steps: c dt max r' = 1.18
-    ("3d", 0, 16, 3),       # 32x32x8, first 3 of 32 steps: c dt max r' = 4.74
+    ("3d", 0, 16, 2),       # 32x32x8, first 2 of 32 steps: c dt max r' = 4.74
 ])
 def test_step_solver_lands_on_the_gradient_flow_root(name, level, samples, steps):
     w = W.MLMC2D_3LVL if name == "2d" else W.SLAB3D_4LVL
@@ -124,18 +124,28 @@ def test_gradient_flow_root_is_a_local_minimum_not_the_lowest_one():
     assert lower
 
 
-@pytest.mark.parametrize("name,level,samples", [("2d", 0, 64), ("3d", 0, 4)])
-def test_selected_root_is_insensitive_to_one_ulp_in_the_field(name, level, samples):
+@pytest.mark.parametrize("name,level,samples,steps", [("2d", 0, 64, 64), ("3d", 0, 4, 16)])
+def test_selected_root_is_insensitive_to_one_ulp_in_the_field(name, level, samples, steps):
+    """The continuation never jumps between basins, so rounding-level changes
+    of the problem leave the selected roots where they are (all 64 steps of
+    64 samples of the 32^2 level; the first 16 of 32 steps of 4 samples of the
+    32x32x8 level)."""
     w = W.MLMC2D_3LVL if name == "2d" else W.SLAB3D_4LVL
     lv = oracle_level(w, level)
 
+    def states(Z):
+        mass, kst = O.assemble(lv, Z)
+        u = O.initial(lv)
+        out = []
+        for _ in range(steps):
+            u, _ = O.step_solve(lv, mass, kst, u)
+            out.append(u)
+        return np.array(out)
+
     def one(i):
         Z = _field(w, level, i)
-        Zp = np.nextafter(Z, np.inf)
-        _, t0, _ = O.solve_sample(lv, Z)
-        _, t1, _ = O.solve_sample(lv, Zp)
-        return float(np.abs(t0 - t1).max())
+        return float(np.abs(states(Z) - states(np.nextafter(Z, np.inf))).max())
 
     with cf.ThreadPoolExecutor(THREADS) as ex:
         diffs = list(ex.map(one, range(samples)))
-    assert max(diffs) <= 1e-9 * lv.T, diffs
+    assert max(diffs) <= 1e-9, diffs
