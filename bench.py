@@ -100,10 +100,13 @@ def oracle_sample_cost(w, pairs, seed=1000, threads=None):
     from paper_1911_06066_gb300 import workloads as W
     threads = threads or (os.cpu_count() or 1)
     levels = []
+    extra = {k: w[k] for k in ("scheme", "stim_kind", "stim_amp", "stim_sigma", "stim_t1", "qoi")
+             if k in w}
     for l in range(w["levels"]):
         n, m = W.level_shape(w, l)
         levels.append(O.make_level(w["dim"], n, m, w["L"], w["T"], w["c"], w["a"], w["s_t"],
-                                   w["s_l0"], w["theta0"], w["theta1"], w["stim_r"], w["stim_c"]))
+                                   w["s_l0"], w["theta0"], w["theta1"], w["stim_r"], w["stim_c"],
+                                   **extra))
     jobs = [(l, i) for l in range(w["levels"]) for i in range(pairs[l])]
     # longest first so the pool drains evenly
     jobs.sort(key=lambda j: -j[0])

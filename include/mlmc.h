@@ -105,7 +105,37 @@ typedef struct {
                             call has the same shape.  Ignored on the legacy default stream
                             (stream NULL), which cannot be captured.  Results are
                             identical to the direct launches.                            */
+  /* The paper's own time discretisation and stimulus (Sec. 3.2, Eq. st-system;
+     Sec. 3.3, Eq. mono_disc; Sec. 4 set-up).  All zero selects the variant
+     above (implicit Euler, the ball as initial state, activation times). */
+  int time_scheme;       /* mlmc_scheme                                                  */
+  int stim_kind;         /* mlmc_stimulus                                                */
+  double stim_amp;       /* MLMC_STIM_PULSE: I_app = stim_amp exp(-|x - stim_c|^2 /      */
+  double stim_sigma;     /*   stim_sigma^2) for 0 <= t < stim_t1, u(x, 0) = 0; each step  */
+  double stim_t1;        /*   takes the current's exact average over the step            */
+  int qoi;               /* mlmc_qoi: the nodal quantity the estimators average          */
 } mlmc_config;
+
+/* Time scheme of the space-time blocks (block row k divided by dt):
+ *   F_k(u) = (M/dt)(u_k - u_{k-1}) + K (theta u_k + (1-theta) u_{k-1})
+ *            - M r(u_k) - M s_k,
+ * theta = 1 implicit Euler (A = M/dt + K, B = -M/dt), theta = 1/2 the
+ * Crank-Nicolson blocks of Sec. 3.2 (A = M/dt + K/2, B = -M/dt + K/2), the
+ * reaction r(u) = c u(1-u)(u-a) at the new time level as in Eq. mono_disc. */
+typedef enum {
+  MLMC_SCHEME_IE = 0,
+  MLMC_SCHEME_CN = 1
+} mlmc_scheme;
+
+typedef enum {
+  MLMC_STIM_BALL = 0,    /* u(x, 0) = 1 for |x - stim_c| < stim_r, else 0          */
+  MLMC_STIM_PULSE = 1    /* u(x, 0) = 0 and the Gaussian applied-current pulse      */
+} mlmc_stimulus;
+
+typedef enum {
+  MLMC_QOI_ACTIVATION = 0,   /* first t with u >= 1/2, linear in t (T if never)   */
+  MLMC_QOI_FINAL_STATE = 1   /* u(x, T), the paper's plotted quantity (Sec. 4)     */
+} mlmc_qoi;
 
 /* Row a7 -- preconditioner of the Newton steps' CG (the paper's Krylov solver
  * is preconditioned by ILU / block Jacobi on CPUs, Sec. 3.5).
@@ -194,6 +224,14 @@ mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi, int n, dou
  * leaves its outputs unwritten and is reported by the next mlmc_run /
  * mlmc_run_more as MLMC_ERR_TIMEOUT. */
 mlmc_status mlmc_kl_tc_workspace_bytes(const mlmc_ctx* ctx, int n, size_t* bytes);
+/* Check of the bounded-wait path (the paper has no counterpart): with polls >=
+ * 0, every tile of the context's later tensor-core KL launches first waits at
+ * most `polls` polls on a barrier that nothing arms -- before it issues any
+ * copy or MMA, so nothing is left in flight -- and takes its timeout exit
+ * (outputs unwritten, counted; the next mlmc_run / mlmc_run_more reports
+ * MLMC_ERR_TIMEOUT, and mlmc_reset clears the count).  polls = -1 restores
+ * normal operation.  The device and the context stay usable throughout. */
+mlmc_status mlmc_check_timeout_path(mlmc_ctx* ctx, long long polls);
 mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
                              void* ws, size_t ws_bytes, void* stream);
 

@@ -42,7 +42,9 @@ class Level(C.Structure):
                 ("a", C.c_double), ("s_t", C.c_double), ("s_l0", C.c_double),
                 ("theta0", C.c_double), ("theta1", C.c_double), ("stim_r", C.c_double),
                 ("stim_c", C.c_double * 3), ("newton_tol", C.c_double),
-                ("newton_max", C.c_int), ("lin_rtol", C.c_double), ("lin_max", C.c_int)]
+                ("newton_max", C.c_int), ("lin_rtol", C.c_double), ("lin_max", C.c_int),
+                ("scheme", C.c_int), ("stim_kind", C.c_int), ("stim_amp", C.c_double),
+                ("stim_sigma", C.c_double), ("stim_t1", C.c_double), ("qoi", C.c_int)]
 
     @property
     def nodes(self):
@@ -64,7 +66,12 @@ class Level(C.Structure):
 
 def make_level(dim, n, m, L, T, c, a, s_t, s_l0, theta0, theta1=None, stim_r=0.1,
                stim_c=(0.0, 0.0, 0.0), newton_tol=1e-12, newton_max=5000,
-               lin_rtol=1e-12, lin_max=5000):
+               lin_rtol=1e-12, lin_max=5000, scheme=0, stim_kind=0, stim_amp=0.0,
+               stim_sigma=1.0, stim_t1=0.0, qoi=0):
+    """One discretisation level.  scheme: 0 implicit Euler, 1 Crank-Nicolson
+    (Sec. 3.2); stim_kind: 0 the ball u0 = 1 (radius stim_r), 1 u0 = 0 and the
+    applied current stim_amp exp(-|x - stim_c|^2 / stim_sigma^2) on [0, stim_t1)
+    (Sec. 4 set-up); qoi: 0 activation time, 1 the final state u(T)."""
     lv = Level()
     lv.dim = dim
     for d in range(3):
@@ -78,6 +85,8 @@ def make_level(dim, n, m, L, T, c, a, s_t, s_l0, theta0, theta1=None, stim_r=0.1
     lv.stim_r = float(stim_r)
     lv.newton_tol, lv.newton_max = float(newton_tol), int(newton_max)
     lv.lin_rtol, lv.lin_max = float(lin_rtol), int(lin_max)
+    lv.scheme, lv.stim_kind, lv.qoi = int(scheme), int(stim_kind), int(qoi)
+    lv.stim_amp, lv.stim_sigma, lv.stim_t1 = float(stim_amp), float(stim_sigma), float(stim_t1)
     return lv
 
 
@@ -100,11 +109,12 @@ def _declare(l):
     l.or_assemble.argtypes = [lp, _dp, _dp, _dp]
     l.or_stiff_apply.argtypes = [lp, _dp, _dp, _dp]
     l.or_initial.argtypes = [lp, _dp]
-    l.or_step_residual.argtypes = [lp, _dp, _dp, _dp, _dp, _dp]
+    l.or_step_residual.argtypes = [lp, _dp, _dp, _dp, _dp, C.c_int, _dp]
+    l.or_stimulus_step.argtypes = [lp, C.c_int, _dp]
     l.or_newton_cg.argtypes = [C.c_int, _dp, _dp, lp, _dp, _dp, _dp, C.POINTER(C.c_int)]
-    l.or_step_solve.argtypes = [lp, _dp, _dp, _dp, _dp, _ip]
-    l.or_step_gradient_flow.argtypes = [lp, _dp, _dp, _dp, C.c_void_p, _dp, C.c_double, C.c_double,
-                                        C.c_int, _ip]
+    l.or_step_solve.argtypes = [lp, _dp, _dp, _dp, C.c_int, _dp, _ip]
+    l.or_step_gradient_flow.argtypes = [lp, _dp, _dp, _dp, C.c_int, C.c_void_p, _dp, C.c_double,
+                                        C.c_double, C.c_int, _ip]
     l.or_solve_sample.argtypes = [lp, _dp, C.c_void_p, _dp, _dp, _ip]
     l.or_slab_residual.argtypes = [lp, _dp, _dp, _dp, _dp]
     l.or_activation.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
@@ -198,11 +208,18 @@ def initial(lv):
     return u0
 
 
-def step_residual(lv, mass, kst, u, u_prev):
+def step_residual(lv, mass, kst, u, u_prev, k=1):
     F = np.zeros(lv.nodes)
     lib().or_step_residual(C.byref(lv), mass, kst, np.ascontiguousarray(u, np.float64),
-                           np.ascontiguousarray(u_prev, np.float64), F)
+                           np.ascontiguousarray(u_prev, np.float64), int(k), F)
     return F
+
+
+def stimulus_step(lv, k):
+    """The applied current averaged over step k at every node."""
+    s = np.zeros(lv.nodes)
+    lib().or_stimulus_step(C.byref(lv), int(k), s)
+    return s
 
 
 def newton_cg(lv, mass, kst, u_lin, F):
@@ -215,17 +232,19 @@ def newton_cg(lv, mass, kst, u_lin, F):
     return d, it, bool(tr.value)
 
 
-def step_solve(lv, mass, kst, u_prev):
-    """One implicit-Euler step.  Returns (u, stats{newton, cg, truncations, halvings})."""
+def step_solve(lv, mass, kst, u_prev, k=1):
+    """Time step k from u_prev.  Returns (u, stats{newton, cg, truncations, halvings})."""
     u = np.zeros(lv.nodes)
     st = np.zeros(4, np.int32)
-    rc = lib().or_step_solve(C.byref(lv), mass, kst, np.ascontiguousarray(u_prev, np.float64), u, st)
+    rc = lib().or_step_solve(C.byref(lv), mass, kst, np.ascontiguousarray(u_prev, np.float64),
+                             int(k), u, st)
     if rc < 0:
         raise RuntimeError("oracle step did not converge")
     return u, dict(zip(("newton", "cg", "truncations", "halvings"), st.tolist()))
 
 
-def step_gradient_flow(lv, mass, kst, u_prev, tau=None, ftol=1e-12, max_pseudo=1000000, v0=None):
+def step_gradient_flow(lv, mass, kst, u_prev, tau=None, ftol=1e-12, max_pseudo=1000000, v0=None,
+                       k=1):
     """Solver-independent root of one implicit-Euler step: the end point of the
     gradient flow M v' = -F(v) of the step energy started at u_prev (the local
     minimum in whose basin u_prev lies; started at v0 instead when given), by
@@ -239,8 +258,8 @@ def step_gradient_flow(lv, mass, kst, u_prev, tau=None, ftol=1e-12, max_pseudo=1
     st = np.zeros(3, np.int32)
     v0c = None if v0 is None else np.ascontiguousarray(v0, np.float64)
     rc = lib().or_step_gradient_flow(C.byref(lv), mass, kst, np.ascontiguousarray(u_prev, np.float64),
-                                     None if v0c is None else v0c.ctypes.data, u, float(tau),
-                                     float(ftol), int(max_pseudo), st)
+                                     int(k), None if v0c is None else v0c.ctypes.data, u,
+                                     float(tau), float(ftol), int(max_pseudo), st)
     if rc < 0:
         raise RuntimeError("gradient flow did not reach the tolerance: %s" % st.tolist())
     return u, dict(zip(("pseudo", "newton", "cg"), st.tolist()))

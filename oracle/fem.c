@@ -120,6 +120,11 @@ void or_stiff_apply(const or_level* lv, const double* Kst, const double* v, doub
 
 void or_initial(const or_level* lv, double* u0) {
   int dim = lv->dim;
+  if (lv->stim_kind == 1) {   /* the applied current starts from rest */
+    int n = or_nodes(lv);
+    for (int i = 0; i < n; ++i) u0[i] = 0.0;
+    return;
+  }
   int Nx = lv->n[0] + 1, Ny = lv->n[1] + 1, Nz = dim == 3 ? lv->n[2] + 1 : 1;
   double h[3] = {lv->L[0] / lv->n[0], lv->L[1] / lv->n[1], dim == 3 ? lv->L[2] / lv->n[2] : 0.0};
   for (int k = 0; k < Nz; ++k)
@@ -129,5 +134,31 @@ void or_initial(const or_level* lv, double* u0) {
         double r2 = 0.0;
         for (int d = 0; d < dim; ++d) r2 += (x[d] - lv->stim_c[d]) * (x[d] - lv->stim_c[d]);
         u0[(k * Ny + j) * Nx + i] = r2 < lv->stim_r * lv->stim_r ? 1.0 : 0.0;
+      }
+}
+
+/* Applied current of the paper's set-up (Sec. 4): I_app(x, t) =
+ * stim_amp exp(-|x - x0|^2 / sigma^2) for 0 <= t < t1, averaged over step k:
+ * the time integral over [t_{k-1}, t_k] (the overlap with [0, t1)) over dt. */
+void or_stimulus_step(const or_level* lv, int k, double* s) {
+  int dim = lv->dim, n = or_nodes(lv);
+  if (lv->stim_kind != 1) {
+    for (int i = 0; i < n; ++i) s[i] = 0.0;
+    return;
+  }
+  double dt = lv->T / lv->m;
+  double a = (k - 1) * dt, b = k * dt;
+  double overlap = fmin(b, lv->stim_t1) - a;
+  if (overlap < 0.0) overlap = 0.0;
+  int Nx = lv->n[0] + 1, Ny = lv->n[1] + 1, Nz = dim == 3 ? lv->n[2] + 1 : 1;
+  double h[3] = {lv->L[0] / lv->n[0], lv->L[1] / lv->n[1], dim == 3 ? lv->L[2] / lv->n[2] : 0.0};
+  for (int kk = 0; kk < Nz; ++kk)
+    for (int j = 0; j < Ny; ++j)
+      for (int i = 0; i < Nx; ++i) {
+        double x[3] = {i * h[0], j * h[1], kk * h[2]};
+        double r2 = 0.0;
+        for (int d = 0; d < dim; ++d) r2 += (x[d] - lv->stim_c[d]) * (x[d] - lv->stim_c[d]);
+        s[(kk * Ny + j) * Nx + i] =
+            overlap > 0.0 ? lv->stim_amp * exp(-r2 / (lv->stim_sigma * lv->stim_sigma)) * overlap / dt : 0.0;
       }
 }

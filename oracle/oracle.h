@@ -54,6 +54,13 @@ typedef struct {
   int newton_max;
   double lin_rtol;    /* CG relative tolerance (preconditioned residual)        */
   int lin_max;
+  int scheme;         /* 0: implicit Euler; 1: Crank-Nicolson diffusion with the
+                         reaction at the new time level (Sec. 3.2-3.3)           */
+  int stim_kind;      /* 0: u0 = 1 in the ball; 1: u0 = 0 and the applied current
+                         I_app = stim_amp exp(-|x - stim_c|^2 / stim_sigma^2)
+                         for 0 <= t < stim_t1 (Sec. 4 set-up)                    */
+  double stim_amp, stim_sigma, stim_t1;
+  int qoi;            /* 0: activation time; 1: the final state u(T)            */
 } or_level;
 
 int or_nodes(const or_level* lv);
@@ -63,9 +70,14 @@ int or_cells(const or_level* lv);
 void or_assemble(const or_level* lv, const double* Z, double* mass, double* Kst);
 void or_stiff_apply(const or_level* lv, const double* Kst, const double* v, double* y);
 void or_initial(const or_level* lv, double* u0);
-/* Per-step residual F(u; u_prev) of implicit Euler for the monodomain problem. */
+/* Per-step residual F(u; u_prev) of step k (1-based; the applied current
+ * enters through its average over [t_{k-1}, t_k]):
+ *   F = (M/dt)(u - u_prev) + K (theta u + (1-theta) u_prev) - M r(u) - M s_k,
+ * theta = 1 (implicit Euler) or 1/2 (Crank-Nicolson). */
 void or_step_residual(const or_level* lv, const double* mass, const double* Kst,
-                      const double* u, const double* u_prev, double* F);
+                      const double* u, const double* u_prev, int k, double* F);
+/* The applied current's average over step k at every node (0 for stim_kind 0). */
+void or_stimulus_step(const or_level* lv, int k, double* s);
 /* Newton direction: Jacobi-PCG on H d = -F, truncated on negative curvature.
  * Returns CG iterations (<0: lin_max reached); *truncated set if truncated. */
 int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* lv,
@@ -73,7 +85,7 @@ int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* l
 /* One implicit-Euler step from up by line-search Newton-CG on the step energy.
  * stats = {newton its, cg its, truncations, halvings}.  Returns its or -1. */
 int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
-                  const double* up, double* u, int* stats);
+                  const double* up, int k, double* u, int* stats);
 /* Solver-independent root of one step: the end point of the mass-metric
  * gradient flow M v' = -F(v) of the step energy from v(0) = up (or v0 when not
  * NULL), integrated by
@@ -81,14 +93,17 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
  * tau (max r' - 1/dt) < 1) until max|F_i| / m_i <= ftol.  stats = {pseudo-steps,
  * Newton iterations, CG iterations}.  Returns pseudo-steps, or -1. */
 int or_step_gradient_flow(const or_level* lv, const double* mass, const double* Kst,
-                          const double* up, const double* v0, double* u, double tau, double ftol,
-                          int max_pseudo, int* stats);
-/* Sequential implicit Euler + Newton for one sample.  u0 = NULL: the stimulus.
- * slab: [m+1][nodes] (slice 0 = u0), t_act: [nodes].
+                          const double* up, int k, const double* v0, double* u, double tau,
+                          double ftol, int max_pseudo, int* stats);
+/* Sequential time stepping for one sample.  u0 = NULL: the configured initial
+ * state (the stimulus ball, or 0 with the applied current).
+ * slab: [m+1][nodes] (slice 0 = u0), t_act: [nodes] = the quantity of
+ * interest (activation times, or u(T) when lv->qoi == 1).
  * Returns total Newton iterations, or -(k) if step k failed to converge. */
 int or_solve_sample(const or_level* lv, const double* Z, const double* u0, double* slab,
                     double* t_act, int* newton_per_step);
-/* All-at-once space-time residual of the slab (Eq. mono_disc, IE blocks). */
+/* All-at-once space-time residual of the slab (Eq. mono_disc; implicit-Euler
+ * or Crank-Nicolson blocks). */
 void or_slab_residual(const or_level* lv, const double* mass, const double* Kst,
                       const double* slab, double* F);
 /* Activation time: first crossing of 0.5, linear in time; T if none. */

@@ -3,14 +3,20 @@
  * Eq. mono_disc) in the implicit-Euler variant, solved step by step.
  * TEST INFRASTRUCTURE ONLY -- see oracle.h.
  *
- * Block row k of the space-time system (k = 1..m, dt = T/m, M lumped):
- *   F_k(u) = (M/dt)(u_k - u_{k-1}) + K u_k - M r(u_k),   r(u) = c u (1-u)(u-a)
- * (the FHN current of Eq. ionic_term written as -c u(1-u)(u-a) on [0,1]).
- * Its Jacobian block (Sec. 3.3) is  H = M/dt + K - M diag(r'(u)),
+ * Block row k of the space-time system (k = 1..m, dt = T/m, M lumped), divided
+ * by dt:
+ *   F_k(u) = (M/dt)(u_k - u_{k-1}) + K (theta u_k + (1-theta) u_{k-1})
+ *            - M r(u_k) - M s_k,                 r(u) = c u (1-u)(u-a)
+ * (the FHN current of Eq. ionic_term written as -c u(1-u)(u-a) on [0,1]);
+ * theta = 1 is implicit Euler, theta = 1/2 the Crank-Nicolson blocks of
+ * Sec. 3.2 (Eq. st-system: A = M + dt/2 K, B = -M + dt/2 K) with the reaction
+ * of Sec. 3.3 (Eq. mono_disc, r(u) = dt (I x M) I_ion(u)) at the new time
+ * level; s_k is the applied current averaged over the step.
+ * Its Jacobian block (Sec. 3.3) is  H = M/dt + theta K - M diag(r'(u)),
  *   r'(u) = c(-3u^2 + 2(1+a)u - a).
  * H is symmetric, so F_k is the gradient of the step energy
- *   E(u) = (u-u_{k-1})^T M (u-u_{k-1}) / (2dt) + u^T K u / 2 - sum_i m_i R(u_i),
- *   R' = r,
+ *   E(u) = (u-u_{k-1})^T M (u-u_{k-1}) / (2dt) + theta u^T K u / 2
+ *          + (1-theta) u_{k-1}^T K u - sum_i m_i (R(u_i) + s_k,i u_i),   R' = r,
  * and H is its Hessian.  When c dt max r' > 1 (max r' = c((1+a)^2/3 - a)) the
  * step has several roots -- local minima of E -- and the paper is silent on
  * which one the scheme means.  The root is defined as the end point of the
@@ -60,21 +66,31 @@ static double rxn_int_diff(double c, double a, double u, double v, double w) {
   return c * w * (-s * q2 / 4.0 + (1.0 + a) * q3 / 3.0 - a * s / 2.0);
 }
 
+static double theta_of(const or_level* lv) { return lv->scheme == 1 ? 0.5 : 1.0; }
+
 void or_step_residual(const or_level* lv, const double* mass, const double* Kst,
-                      const double* u, const double* u_prev, double* F) {
+                      const double* u, const double* u_prev, int k, double* F) {
   int n = or_nodes(lv);
-  double dt = lv->T / lv->m;
+  double dt = lv->T / lv->m, th = theta_of(lv);
+  double* Kp = malloc(sizeof(double) * n);
+  double* sk = malloc(sizeof(double) * n);
   or_stiff_apply(lv, Kst, u, F);
+  or_stiff_apply(lv, Kst, u_prev, Kp);
+  or_stimulus_step(lv, k, sk);
   for (int i = 0; i < n; ++i)
-    F[i] += mass[i] / dt * (u[i] - u_prev[i]) - mass[i] * rxn(lv->c, lv->a, u[i]);
+    F[i] = th * F[i] + (1.0 - th) * Kp[i] + mass[i] / dt * (u[i] - u_prev[i]) -
+           mass[i] * rxn(lv->c, lv->a, u[i]) - mass[i] * sk[i];
+  free(Kp); free(sk);
 }
 
+/* y = H v, H = M/dt + theta K - M diag(r'(u_lin)) */
 static void hess_apply(const or_level* lv, const double* mass, const double* Kst,
                        const double* u_lin, const double* v, double* y) {
   int n = or_nodes(lv);
-  double dt = lv->T / lv->m;
+  double dt = lv->T / lv->m, th = theta_of(lv);
   or_stiff_apply(lv, Kst, v, y);
-  for (int i = 0; i < n; ++i) y[i] += (mass[i] / dt - mass[i] * rxn_d(lv->c, lv->a, u_lin[i])) * v[i];
+  for (int i = 0; i < n; ++i)
+    y[i] = th * y[i] + (mass[i] / dt - mass[i] * rxn_d(lv->c, lv->a, u_lin[i])) * v[i];
 }
 
 static double dot(int n, const double* a, const double* b) {
@@ -99,7 +115,7 @@ static int shifted_cg(int n, const double* mass, const double* Kst, const or_lev
   double* q = malloc(sizeof(double) * n);
   for (int i = 0; i < n; ++i) {
     double dg = mass[i] * (shift + 1.0 / dt) - mass[i] * rxn_d(lv->c, lv->a, u_lin[i]) +
-                Kst[(size_t)i * no + ctr];
+                theta_of(lv) * Kst[(size_t)i * no + ctr];
     pinv[i] = 1.0 / fabs(dg);
   }
   memset(d, 0, sizeof(double) * n);
@@ -137,29 +153,36 @@ int or_newton_cg(int n, const double* mass, const double* Kst, const or_level* l
   return shifted_cg(n, mass, Kst, lv, u_lin, 0.0, F, d, truncated);
 }
 
-/* E(u + alpha d) - E(u), given Ku = K u and Kd = K d. */
+/* E(u + alpha d) - E(u) for the step energy
+ *   E(u) = (u-up)^T M (u-up)/(2dt) + theta u^T K u/2 + (1-theta) up^T K u
+ *          - sum_i m_i (R(u_i) + s_i u_i),
+ * given Ku = K u, Kd = K d, Kp = K up and the step's applied current s. */
 static double energy_change(const or_level* lv, int n, const double* mass, const double* u,
                             const double* up, const double* d, const double* Ku,
-                            const double* Kd, double alpha) {
-  double dt = lv->T / lv->m;
+                            const double* Kd, const double* Kp, const double* sk, double alpha) {
+  double dt = lv->T / lv->m, th = theta_of(lv);
   double s = 0.0;
   for (int i = 0; i < n; ++i) {
     double w = alpha * d[i];
     double v = u[i] + w;
     s += mass[i] * w * (2.0 * (u[i] - up[i]) + w) / (2.0 * dt);
-    s += w * Ku[i] + 0.5 * w * alpha * Kd[i];
-    s -= mass[i] * rxn_int_diff(lv->c, lv->a, u[i], v, w);
+    s += th * (w * Ku[i] + 0.5 * w * alpha * Kd[i]) + (1.0 - th) * w * Kp[i];
+    s -= mass[i] * rxn_int_diff(lv->c, lv->a, u[i], v, w) + mass[i] * sk[i] * w;
   }
   return s;
 }
 
 int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
-                  const double* up, double* u, int* stats) {
+                  const double* up, int k, double* u, int* stats) {
   int n = or_nodes(lv);
   double* F = malloc(sizeof(double) * n);
   double* d = malloc(sizeof(double) * n);
   double* Ku = malloc(sizeof(double) * n);
   double* Kd = malloc(sizeof(double) * n);
+  double* Kp = malloc(sizeof(double) * n);
+  double* sk = malloc(sizeof(double) * n);
+  or_stiff_apply(lv, Kst, up, Kp);
+  or_stimulus_step(lv, k, sk);
   int it, conv = 0, cg_total = 0, trunc_total = 0, halvings = 0;
   double dt = lv->T / lv->m;
   double rmax = lv->c * ((1.0 + lv->a) * (1.0 + lv->a) / 3.0 - lv->a);
@@ -168,7 +191,7 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
   int newton_phase = 0;
   memcpy(u, up, sizeof(double) * n);
   for (it = 1; it <= lv->newton_max; ++it) {
-    or_step_residual(lv, mass, Kst, u, up, F);
+    or_step_residual(lv, mass, Kst, u, up, k, F);
     int tr;
     if (flow) {
       /* linearly implicit pseudo-step of the gradient flow M v' = -F(v):
@@ -225,7 +248,7 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
       or_stiff_apply(lv, Kst, u, Ku);
       or_stiff_apply(lv, Kst, d, Kd);
       for (int h = 0; h < 40; ++h) {
-        double dE = energy_change(lv, n, mass, u, up, d, Ku, Kd, alpha);
+        double dE = energy_change(lv, n, mass, u, up, d, Ku, Kd, Kp, sk, alpha);
         if (dE <= 1e-4 * alpha * gd) break;
         alpha *= 0.5;
         ++halvings;
@@ -235,7 +258,7 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
     if (dmax <= lv->newton_tol) { conv = 1; break; }
   }
   if (stats) { stats[0] = it; stats[1] = cg_total; stats[2] = trunc_total; stats[3] = halvings; }
-  free(F); free(d); free(Ku); free(Kd);
+  free(F); free(d); free(Ku); free(Kd); free(Kp); free(sk);
   return conv ? it : -1;
 }
 
@@ -271,7 +294,7 @@ static int prox_cg(int n, const double* mass, const double* Kst, const or_level*
   double* q = malloc(sizeof(double) * n);
   for (int i = 0; i < n; ++i)
     pinv[i] = 1.0 / (mass[i] * (inv_tau + 1.0 / dt - rxn_d(lv->c, lv->a, w[i])) +
-                     Kst[(size_t)i * no + ctr]);
+                     theta_of(lv) * Kst[(size_t)i * no + ctr]);
   memset(d, 0, sizeof(double) * n);
   for (int i = 0; i < n; ++i) { r[i] = -G[i]; z[i] = pinv[i] * r[i]; p[i] = z[i]; }
   double rz = dot(n, r, z), r0 = sqrt(rz);
@@ -296,8 +319,8 @@ done:
 }
 
 int or_step_gradient_flow(const or_level* lv, const double* mass, const double* Kst,
-                          const double* up, const double* v0, double* u, double tau, double ftol,
-                          int max_pseudo, int* stats) {
+                          const double* up, int k, const double* v0, double* u, double tau,
+                          double ftol, int max_pseudo, int* stats) {
   int n = or_nodes(lv);
   double dt = lv->T / lv->m;
   double rmax = lv->c * ((1.0 + lv->a) * (1.0 + lv->a) / 3.0 - lv->a);
@@ -308,12 +331,16 @@ int or_step_gradient_flow(const or_level* lv, const double* mass, const double* 
   double* d = malloc(sizeof(double) * n);
   double* Ku = malloc(sizeof(double) * n);
   double* Kd = malloc(sizeof(double) * n);
+  double* Kp = malloc(sizeof(double) * n);
+  double* sk = malloc(sizeof(double) * n);
+  or_stiff_apply(lv, Kst, up, Kp);
+  or_stimulus_step(lv, k, sk);
   int j, ok = 0, newton = 0, cg = 0;
   double inv_tau = 1.0 / tau;
   memcpy(u, v0 ? v0 : up, sizeof(double) * n);
   const double flow_tol = ftol > 1e-8 ? ftol : 1e-8;
   for (j = 0; j <= max_pseudo; ++j) {
-    or_step_residual(lv, mass, Kst, u, up, F);
+    or_step_residual(lv, mass, Kst, u, up, k, F);
     double fm = 0.0;
     for (int i = 0; i < n; ++i) if (fabs(F[i]) / mass[i] > fm) fm = fabs(F[i]) / mass[i];
     if (fm <= flow_tol) { ok = 1; break; }
@@ -323,7 +350,7 @@ int or_step_gradient_flow(const or_level* lv, const double* mass, const double* 
        P(w) = E(w) + (w - v)^T M (w - v) / (2 tau),  gradient F(w) + M (w - v) / tau */
     int conv = 0;
     for (int it = 0; it < 100 && !conv; ++it) {
-      if (it > 0) or_step_residual(lv, mass, Kst, u, up, F);
+      if (it > 0) or_step_residual(lv, mass, Kst, u, up, k, F);
       for (int i = 0; i < n; ++i) G[i] = F[i] + mass[i] * inv_tau * (u[i] - v[i]);
       int c1 = prox_cg(n, mass, Kst, lv, u, inv_tau, G, d);
       if (c1 < 0) goto fail;
@@ -337,7 +364,7 @@ int or_step_gradient_flow(const or_level* lv, const double* mass, const double* 
         or_stiff_apply(lv, Kst, u, Ku);
         or_stiff_apply(lv, Kst, d, Kd);
         for (int h = 0; h < 60; ++h) {
-          double dP = energy_change(lv, n, mass, u, up, d, Ku, Kd, alpha);
+          double dP = energy_change(lv, n, mass, u, up, d, Ku, Kd, Kp, sk, alpha);
           for (int i = 0; i < n; ++i) {
             double w = alpha * d[i];
             dP += mass[i] * w * (2.0 * (u[i] - v[i]) + w) * 0.5 * inv_tau;
@@ -355,7 +382,7 @@ int or_step_gradient_flow(const or_level* lv, const double* mass, const double* 
     /* Newton polish at the nondegenerate minimum the flow has reached */
     ok = 0;
     for (int it = 0; it < 50; ++it) {
-      or_step_residual(lv, mass, Kst, u, up, F);
+      or_step_residual(lv, mass, Kst, u, up, k, F);
       double fm = 0.0;
       for (int i = 0; i < n; ++i) if (fabs(F[i]) / mass[i] > fm) fm = fabs(F[i]) / mass[i];
       if (fm <= ftol) { ok = 1; break; }
@@ -368,7 +395,7 @@ int or_step_gradient_flow(const or_level* lv, const double* mass, const double* 
   }
 fail:
   if (stats) { stats[0] = j; stats[1] = newton; stats[2] = cg; }
-  free(v); free(F); free(G); free(d); free(Ku); free(Kd);
+  free(v); free(F); free(G); free(d); free(Ku); free(Kd); free(Kp); free(sk);
   return ok ? j : -1;
 }
 
@@ -401,12 +428,15 @@ int or_solve_sample(const or_level* lv, const double* Z, const double* u0, doubl
   int total = 0, ret = 0;
   for (int k = 1; k <= lv->m && ret == 0; ++k) {
     int st[4];
-    int it = or_step_solve(lv, mass, Kst, slab + (size_t)(k - 1) * n, slab + (size_t)k * n, st);
+    int it = or_step_solve(lv, mass, Kst, slab + (size_t)(k - 1) * n, k, slab + (size_t)k * n, st);
     if (newton_per_step) newton_per_step[k - 1] = st[0];
     total += st[0];
     if (it < 0) ret = -k;
   }
-  if (t_act) or_activation(n, lv->m, lv->T / lv->m, lv->T, slab, t_act);
+  if (t_act) {
+    if (lv->qoi == 1) memcpy(t_act, slab + (size_t)lv->m * n, sizeof(double) * n);
+    else or_activation(n, lv->m, lv->T / lv->m, lv->T, slab, t_act);
+  }
   free(mass); free(Kst);
   return ret ? ret : total;
 }
@@ -415,6 +445,6 @@ void or_slab_residual(const or_level* lv, const double* mass, const double* Kst,
                       const double* slab, double* F) {
   int n = or_nodes(lv);
   for (int k = 1; k <= lv->m; ++k)
-    or_step_residual(lv, mass, Kst, slab + (size_t)k * n, slab + (size_t)(k - 1) * n,
+    or_step_residual(lv, mass, Kst, slab + (size_t)k * n, slab + (size_t)(k - 1) * n, k,
                      F + (size_t)(k - 1) * n);
 }

@@ -32,11 +32,16 @@ class mlmc_config(C.Structure):
                 ("precision", C.c_int), ("newton_tol", C.c_double), ("newton_max", C.c_int),
                 ("lin_rtol", C.c_double), ("lin_max", C.c_int), ("solver", C.c_int),
                 ("mixed_cdr_max", C.c_double), ("cluster_size", C.c_int), ("precond", C.c_int),
-                ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int), ("use_graph", C.c_int)]
+                ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int), ("use_graph", C.c_int),
+                ("time_scheme", C.c_int), ("stim_kind", C.c_int), ("stim_amp", C.c_double),
+                ("stim_sigma", C.c_double), ("stim_t1", C.c_double), ("qoi", C.c_int)]
 
 
 MLMC_SOLVER_AUTO, MLMC_SOLVER_BLOCK, MLMC_SOLVER_CLUSTER = 0, 1, 2
 MLMC_PRECOND_JACOBI, MLMC_PRECOND_GMG = 0, 1
+MLMC_SCHEME_IE, MLMC_SCHEME_CN = 0, 1
+MLMC_STIM_BALL, MLMC_STIM_PULSE = 0, 1
+MLMC_QOI_ACTIVATION, MLMC_QOI_FINAL_STATE = 0, 1
 
 
 class mlmc_sample_info(C.Structure):
@@ -106,6 +111,7 @@ def lib():
                                   vp, vp, vp], ip),
             "mlmc_diagnostics": ([vp, vp, vp, vp, vp], ip),
             "mlmc_level_stats": ([vp, vp], ip),
+            "mlmc_check_timeout_path": ([vp, C.c_longlong], ip),
             "mlmc_get_state": ([vp, vp, vp, vp, vp, vp], ip),
             "mlmc_set_state": ([vp, vp, vp, vp, vp, vp], ip),
             "mlmc_merge_states": ([ip, i64, vp, vp, vp, vp, vp, vp, vp, vp], ip),
@@ -140,7 +146,7 @@ def exported_symbols():
             "mlmc_slab_residual",
             "mlmc_activation", "mlmc_sample_level", "mlmc_accumulate", "mlmc_reset",
             "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_run_more",
-            "mlmc_run_to_rmse", "mlmc_diagnostics", "mlmc_level_stats", "mlmc_get_state", "mlmc_set_state", "mlmc_merge_states",
+            "mlmc_run_to_rmse", "mlmc_diagnostics", "mlmc_level_stats", "mlmc_check_timeout_path", "mlmc_get_state", "mlmc_set_state", "mlmc_merge_states",
             "mlmc_autotune", "mlmc_get_layout", "mlmc_set_layout", "mlmc_server_create",
             "mlmc_server_submit", "mlmc_server_poll", "mlmc_server_drain", "mlmc_server_stats",
             "mlmc_server_clock", "mlmc_server_estimate", "mlmc_server_error",
@@ -239,6 +245,14 @@ def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, 
     c.cluster_size = cluster_size
     c.precond, c.mg_nu, c.mg_coarse_sweeps = precond, mg_nu, mg_coarse_sweeps
     c.use_graph = 1 if use_graph else 0
+    # the paper's time scheme, applied-current pulse and final-state QoI (the
+    # workload keys scheme / stim_kind / stim_amp / stim_sigma / stim_t1 / qoi)
+    c.time_scheme = int(w.get("scheme", MLMC_SCHEME_IE))
+    c.stim_kind = int(w.get("stim_kind", MLMC_STIM_BALL))
+    c.stim_amp = float(w.get("stim_amp", 0.0))
+    c.stim_sigma = float(w.get("stim_sigma", 1.0))
+    c.stim_t1 = float(w.get("stim_t1", 0.0))
+    c.qoi = int(w.get("qoi", MLMC_QOI_ACTIVATION))
     return c
 
 
@@ -462,6 +476,11 @@ class Context:
         return dict(N_l=N, mean=mean, var=var, V_l=V, C_l=Cl, rmse=rmse.value, bias=bias.value,
                     reached=st == MLMC_OK,
                     message=lib().mlmc_last_error(self.h).decode() if st != MLMC_OK else "")
+
+    def check_timeout_path(self, polls):
+        """polls >= 0: the tensor-core KL tiles time out on purpose (before
+        issuing any work); -1: normal operation (mlmc_check_timeout_path)."""
+        self._check(lib().mlmc_check_timeout_path(self.h, int(polls)))
 
     def level_stats(self):
         """Per-level solve statistics (mlmc_level_stats): a list of dicts."""

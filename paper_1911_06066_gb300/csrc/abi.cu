@@ -115,6 +115,15 @@ static bool check_ws(mlmc_ctx* ctx, void* ws, size_t have, size_t need) {
   return true;
 }
 
+// Time scheme, stimulus and QoI fields of a configuration.
+bool mlmc::model_config_ok(const mlmc_config& c) {
+  if (c.time_scheme != MLMC_SCHEME_IE && c.time_scheme != MLMC_SCHEME_CN) return false;
+  if (c.qoi != MLMC_QOI_ACTIVATION && c.qoi != MLMC_QOI_FINAL_STATE) return false;
+  if (c.stim_kind == MLMC_STIM_BALL) return true;
+  return c.stim_kind == MLMC_STIM_PULSE && c.stim_sigma > 0.0 && c.stim_t1 >= 0.0 &&
+         c.stim_amp == c.stim_amp;
+}
+
 // Geometry of level `level` of a configuration: n0[d] 2^level cells per axis,
 // m0 2^level implicit-Euler steps.  False (and a message) when a size does not
 // fit the kernels' index types.
@@ -156,6 +165,12 @@ void mlmc::derive_physics(const mlmc_config& c, Physics* out) {
   ph.Lz = c.dim == 3 ? c.L[2] : 1.0;
   ph.stim_r2 = c.stim_r * c.stim_r;
   for (int d = 0; d < 3; ++d) ph.stim_c[d] = c.stim_c[d];
+  ph.theta = c.time_scheme == MLMC_SCHEME_CN ? 0.5 : 1.0;
+  ph.stim_kind = c.stim_kind;
+  ph.stim_amp = c.stim_amp;
+  ph.stim_isig2 = c.stim_kind == MLMC_STIM_PULSE ? 1.0 / (c.stim_sigma * c.stim_sigma) : 0.0;
+  ph.stim_t1 = c.stim_t1;
+  ph.qoi = c.qoi;
   *out = ph;
 }
 
@@ -204,6 +219,7 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
     return fail(nullptr, MLMC_ERR_ARG, "unknown preconditioner");
   if (c.mg_nu < 0 || c.mg_nu > 8 || c.mg_coarse_sweeps < 0 || c.mg_coarse_sweeps > 64)
     return fail(nullptr, MLMC_ERR_ARG, "mg_nu must be 0..8 and mg_coarse_sweeps 0..64");
+  if (!model_config_ok(c)) return fail(nullptr, MLMC_ERR_ARG, "time scheme, stimulus or QoI out of range");
 
   mlmc_ctx* ctx = new mlmc_ctx();
   ctx->cfg = c;
@@ -371,7 +387,7 @@ extern "C" mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* 
   CK(ctx, launch_kl_field_tc(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_idx,
                              ctx->d_phi32[level][0], ctx->d_phi32[level][1],
                              ctx->d_phi32[level][2], xi, n, Z, ws, ctx->d_cnt + CNT_TC_TIMEOUT,
-                             (cudaStream_t)stream));
+                             ctx->tc_check_limit, (cudaStream_t)stream));
   ctx->launches += 2;
   return MLMC_OK;
 }
@@ -875,6 +891,14 @@ static mlmc_status fill_stats(mlmc_ctx* ctx, double* stats) {
     snprintf(b, sizeof b, "%llu sample solves did not converge", tot[0]);
     return fail(ctx, MLMC_ERR_NOT_CONVERGED, b);
   }
+  return MLMC_OK;
+}
+
+// Check of the bounded-wait path of the tensor-core KL kernel.
+extern "C" mlmc_status mlmc_check_timeout_path(mlmc_ctx* ctx, long long polls) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (polls < -1) return fail(ctx, MLMC_ERR_ARG, "mlmc_check_timeout_path: polls must be >= -1");
+  ctx->tc_check_limit = polls;
   return MLMC_OK;
 }
 

@@ -80,11 +80,14 @@ __global__ void assemble_kernel(LevelDesc lv, Physics ph, const double* __restri
               K[o] += element_entry(DIM, D, lv.h, a, b);
             }
       }
+  // stored times theta (1 implicit Euler, 1/2 Crank-Nicolson): the Hessian's
+  // stiffness part, and with (1-theta)/theta the explicit part of the residual
   int64_t base = (int64_t)s * NO * lv.nodes + A;
 #pragma unroll
   for (int o = 0; o < NO; ++o) {
-    coef64[base + (int64_t)o * lv.nodes] = K[o];
-    if (coef32) coef32[base + (int64_t)o * lv.nodes] = (float)K[o];
+    const double k = ph.theta * K[o];
+    coef64[base + (int64_t)o * lv.nodes] = k;
+    if (coef32) coef32[base + (int64_t)o * lv.nodes] = (float)k;
   }
 }
 

@@ -46,6 +46,7 @@ struct mlmc_ctx {
   bool capturing = false;
   cudaGraphExec_t graph_exec = nullptr;
   long graph_runs = 0;
+  long long tc_check_limit = -1;   // mlmc_check_timeout_path: -1 normal operation
   std::string err;
 };
 

@@ -33,7 +33,25 @@ struct Physics {
   double stim_r2;        // squared stimulus radius
   double stim_c[3];
   const double* stim_ps; // per-sample stimulus centres, device [n][3], or NULL
+  // time scheme: theta = 1 implicit Euler, 1/2 Crank-Nicolson (the couplings
+  // are assembled times theta; the residual adds (1-theta)/theta times the
+  // scaled stencil of u_{k-1})
+  double theta;
+  // stimulus kind 1: u0 = 0 and the applied current amp exp(-|x - c|^2 isig2)
+  // on 0 <= t < t1 (kind 0: u0 = 1 in the ball of radius sqrt(stim_r2))
+  int stim_kind;
+  double stim_amp, stim_isig2, stim_t1;
+  int qoi;               // 0: activation time; 1: the final state u(T)
 };
+
+// The applied current averaged over step k (1-based) at squared distance r2
+// from the centre: amp exp(-r2 isig2) |[t_{k-1}, t_k] ∩ [0, t1)| / dt.
+__host__ __device__ inline double stim_step_scale(const Physics& p, int k, double dt) {
+  if (p.stim_kind != 1) return 0.0;
+  const double a = (k - 1) * dt, b = k * dt;
+  const double ov = (b < p.stim_t1 ? b : p.stim_t1) - a;
+  return ov > 0.0 ? p.stim_amp * ov / dt : 0.0;
+}
 
 struct SolverParams {
   double newton_tol;
@@ -71,6 +89,7 @@ inline bool level_has_several_roots(double c, double a, double dt) {
 // Configuration-derived quantities shared by mlmc_create, mlmc_solve and
 // mlmc_solve_noalloc (defined in abi.cu).
 bool derive_level(const mlmc_config& c, int level, LevelDesc* lv, std::string* err);
+bool model_config_ok(const mlmc_config& c);
 void derive_physics(const mlmc_config& c, Physics* ph);
 // FP32 inner solves are used only where the step Jacobian is at most mildly
 // indefinite: MLMC_PREC_MIXED and c dt max r' <= mixed_cdr_max (default 2).
@@ -136,6 +155,16 @@ __device__ inline void node_ijk(const LevelDesc& lv, int64_t A, int& i, int& j, 
   k = (int)(r / lv.N[1]);
 }
 
+// Spatial shape of the applied current at node (i, j, k): exp(-|x - c|^2 isig2),
+// c the (per-sample) stimulus centre sc.
+__device__ inline double stim_shape(const Physics& p, const LevelDesc& lv, const double* sc, int i,
+                                    int j, int k) {
+  const double x[3] = {i * lv.h[0], j * lv.h[1], k * lv.h[2]};
+  double r2 = 0.0;
+  for (int d = 0; d < lv.dim; ++d) r2 += (x[d] - sc[d]) * (x[d] - sc[d]);
+  return exp(-r2 * p.stim_isig2);
+}
+
 // Reaction r(u) = c u (1-u)(u-a) and its derivative.
 __device__ inline double rxn(const Physics& p, double u) { return p.c * u * (1.0 - u) * (u - p.a); }
 __device__ inline double rxn_d(const Physics& p, double u) {
@@ -152,12 +181,15 @@ cudaError_t launch_kl_field(const LevelDesc& lv, int M, const double* sqrt_lam, 
 // split-TF32 products, FP32 accumulation in tensor memory, FP64 output.  err
 // (device) counts CTAs whose bounded wait for the tensor cores ran out.
 // ws: kl_tc_workspace_bytes(M, n) bytes (the prepared B operand), 256-byte
-// aligned; phi_*: the 1D mode tables in FP32.
+// aligned; phi_*: the 1D mode tables in FP32.  check_limit >= 0 (a check of
+// the timeout path): every CTA first waits at most that many polls on a
+// barrier nothing arms, before issuing any copy or MMA, and takes its timeout
+// exit; -1 for normal operation.
 size_t kl_tc_workspace_bytes(int M, int n);
 cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
                                const float* phi_x, const float* phi_y, const float* phi_z,
                                const double* xi, int n, double* Z, void* ws,
-                               unsigned long long* err, cudaStream_t st);
+                               unsigned long long* err, long long check_limit, cudaStream_t st);
 cudaError_t preload_kl_tc();
 cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,
                             double* coef64, float* coef32, cudaStream_t st);

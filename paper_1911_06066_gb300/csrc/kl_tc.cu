@@ -76,8 +76,9 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = TC_SPIN_LIMIT) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(TC_THREADS)
 kl_field_tc_kernel(LevelDesc lv, int M, int nt, const int* __restrict__ idx,
                    const float* __restrict__ phx, const float* __restrict__ phy,
                    const float* __restrict__ phz, const unsigned char* __restrict__ bprep, int n,
-                   double* __restrict__ Z, unsigned long long* err) {
+                   double* __restrict__ Z, unsigned long long* err, long long check_limit) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   // align the operand tiles to 1024 bytes (the swizzle atom)
   unsigned char* sm = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
@@ -234,6 +235,14 @@ kl_field_tc_kernel(LevelDesc lv, int M, int nt, const int* __restrict__ idx,
   bool ok = true;
   int issued = 0;     // chunks whose MMAs were committed
   int stuck = -1;     // chunk whose operand copy did not land in time
+  if (check_limit >= 0) {
+    // Check of the bounded-wait path: before any copy or MMA of this CTA is
+    // issued, wait at most check_limit polls on the first stage's 'full'
+    // barrier, which nothing has armed yet -- the wait runs out, nothing is
+    // in flight, and the CTA takes the timeout exit below.
+    if (tid == 0) ok = mbar_wait(smem_addr(&full[0]), 0u, check_limit);
+    ok = __syncthreads_and(ok);
+  }
   for (int c = 0; c < chunks && ok; ++c) {
     const int st = c & 1;
     if (c >= 2) ok = mbar_wait(smem_addr(&done[st]), (uint32_t)(((c - 2) >> 1) & 1));
@@ -365,7 +374,7 @@ cudaError_t preload_kl_tc() {
 cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
                                const float* phi_x, const float* phi_y, const float* phi_z,
                                const double* xi, int n, double* Z, void* ws,
-                               unsigned long long* err, cudaStream_t st) {
+                               unsigned long long* err, long long check_limit, cudaStream_t st) {
   if (n == 0 || lv.cells == 0) return cudaSuccess;
   const int nt = kl_tc_nt(n);
   const int chunks = (M + TC_KC - 1) / TC_KC, tiles = (n + nt - 1) / nt;
@@ -379,7 +388,8 @@ cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_la
   if (mt > 0x7fffffff || tiles > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)mt, (unsigned)tiles);
   kl_field_tc_kernel<<<grid, TC_THREADS, smem, st>>>(lv, M, nt, idx, phi_x, phi_y, phi_z,
-                                                     (const unsigned char*)ws, n, Z, err);
+                                                     (const unsigned char*)ws, n, Z, err,
+                                                     check_limit);
   return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int level, con
     return reject(MLMC_ERR_ARG, "invalid configuration");
   if (c.precision != MLMC_PREC_FP64 && c.precision != MLMC_PREC_MIXED)
     return reject(MLMC_ERR_ARG, "unknown precision");
+  if (!model_config_ok(c)) return reject(MLMC_ERR_ARG, "time scheme, stimulus or QoI out of range");
   if (n < 0 || n > 65535 || (n > 0 && (!Z || !t_act))) return reject(MLMC_ERR_ARG, "bad arguments");
 
   // level geometry and parameters, derived by the same helpers as mlmc_create

@@ -1,9 +1,10 @@
 // Row a4 over the whole slab and row a8 from a stored slab.
 //
 // slab_residual: the all-at-once space-time residual (Sec. 3.3, Eq. mono_disc
-// with the implicit-Euler blocks of Eq. system_C), every (sample, slice, node)
-// in one launch:
-//   F[s][k-1][A] = (K u_k)_A + (M_A/dt)(u_k - u_{k-1})_A - M_A r(u_k,A),  k = 1..m,
+// with the blocks of Eq. system_C: implicit Euler or Crank-Nicolson, Sec. 3.2),
+// every (sample, slice, node) in one launch:
+//   F[s][k-1][A] = (K (theta u_k + (1-theta) u_{k-1}))_A + (M_A/dt)(u_k - u_{k-1})_A
+//                  - M_A r(u_k,A) - M_A s_k,A,  k = 1..m,
 // and res_max[s] = max |F| / M_A, the convergence certificate of the slab.
 // Memory-bound stream: reads u_k, u_{k-1} (the latter from L2/L1 when adjacent
 // slices are processed by neighbouring blocks) and the couplings, writes F.
@@ -41,11 +42,28 @@ __global__ void slab_residual_kernel(LevelDesc lv, Physics ph, const double* __r
       B = B < 0 ? 0 : (B >= N ? N - 1 : B);
       ku += c[(int64_t)o * N + A] * u[B];
     }
+    // Crank-Nicolson: (1-theta)/theta times the theta-scaled stencil of u_{k-1}
+    const double c_up = (1.0 - ph.theta) / ph.theta;
+    if (c_up != 0.0) {
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+        int64_t B = A + dx + (int64_t)lv.N[0] * (dy + (int64_t)lv.N[1] * dz);
+        B = B < 0 ? 0 : (B >= N ? N - 1 : B);
+        ku += c_up * c[(int64_t)o * N + A] * up[B];
+      }
+    }
     int i, j, kk;
     node_ijk(lv, A, i, j, kk);
     double mA = lumped_mass(lv, i, j, kk);
     double uA = u[A];
     double f = ku + mA / lv.dt * (uA - up[A]) - mA * rxn(ph, uA);
+    const double src = stim_step_scale(ph, k, lv.dt);
+    if (src != 0.0) {
+      double sc[3];
+      for (int d = 0; d < 3; ++d) sc[d] = ph.stim_ps ? ph.stim_ps[3 * s + d] : ph.stim_c[d];
+      f -= mA * src * stim_shape(ph, lv, sc, i, j, kk);
+    }
     if (F) F[(int64_t)s * per_sample + g] = f;
     rel = fabs(f) / mA;
   }

@@ -138,7 +138,7 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
     double x[3] = {i * lv.h[0], j * lv.h[1], k * lv.h[2]};
     double r2 = 0.0;
     for (int dd = 0; dd < DIM; ++dd) r2 += (x[dd] - sc[dd]) * (x[dd] - sc[dd]);
-    double v = r2 < ph.stim_r2 ? 1.0 : 0.0;
+    double v = ph.stim_kind == 0 && r2 < ph.stim_r2 ? 1.0 : 0.0;
     u0[A] = v;
     ta[A] = v >= 0.5 ? 0.0 : -1.0;
   }
@@ -151,6 +151,8 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
     double* u = sl ? sl + (int64_t)step * N : ub + (int64_t)(step & 1) * N;
     for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) u[A] = up[A];
     __syncthreads();
+    const double c_up = (1.0 - ph.theta) / ph.theta;      // Crank-Nicolson: explicit part
+    const double src_scale = stim_step_scale(ph, step, dt);
     double tau = sp.tau0, sw = FLOW_NEWTON;
     bool newton_phase = false;
     bool conv = false, lin_fail = false;
@@ -170,7 +172,12 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
         node_ijk(lv, A, i, j, k);
         double mA = lumped_mass(lv, i, j, k);
         double uA = u[A];
+        // Ku: the part of the residual linear in u and the explicit terms
+        // (theta K u + (1-theta) K u_{k-1} - M s_k); the energy line search
+        // uses it as the linear coefficient of its step length
         double ku = stencil<DIM, double, double, double>(lv, c64, u, A);
+        if (c_up != 0.0) ku += c_up * stencil<DIM, double, double, double>(lv, c64, up, A);
+        if (src_scale != 0.0) ku -= mA * src_scale * stim_shape(ph, lv, sc, i, j, k);
         Ku[A] = ku;
         double f = ku + mA * inv_dt * (uA - up[A]) - mA * rxn(ph, uA);
         F[A] = f;
@@ -312,8 +319,15 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
     }
     // the next step reads u as up after the sync at its start
   }
-  for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS)
-    if (ta[A] < 0.0) ta[A] = lv.T;
+  {
+    // the quantity of interest: activation times (T where never reached), or
+    // the final state u(T)
+    const double* ufin = sl ? sl + (int64_t)lv.m * N : ub + (int64_t)(lv.m & 1) * N;
+    for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) {
+      if (ph.qoi == 1) ta[A] = ufin[A];
+      else if (ta[A] < 0.0) ta[A] = lv.T;
+    }
+  }
   if (counters && threadIdx.x == 0) {
     if (status != MLMC_OK) atomicAdd(counters, 1ull);
     atomicAdd(counters + 1, (unsigned long long)cg_total * (unsigned long long)N);

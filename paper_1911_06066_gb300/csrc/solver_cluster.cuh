@@ -345,7 +345,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     double x[3] = {CI(c) * lv.h[0], CJ(c) * lv.h[1], CK_(c) * lv.h[2]};
     double r2 = 0.0;
     for (int dd = 0; dd < DIM; ++dd) r2 += (x[dd] - sc[dd]) * (x[dd] - sc[dd]);
-    double v = r2 < ph.stim_r2 ? 1.0 : 0.0;
+    double v = ph.stim_kind == 0 && r2 < ph.stim_r2 ? 1.0 : 0.0;
     ubuf0[a] = v;
     ta[A] = v >= 0.5 ? 0.0 : -1.0;
     if (sl) sl[A] = v;
@@ -362,6 +362,11 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     double* u = (step & 1) ? ubuf1 : ubuf0;
     const double* up = (step & 1) ? ubuf0 : ubuf1;
     const View<double>& uv = (step & 1) ? uv1 : uv0;
+    const View<double>& upv = (step & 1) ? uv0 : uv1;
+    // explicit part of the residual: (1-theta)/theta times the (theta-scaled)
+    // stencil of u_{k-1} (Crank-Nicolson), and the applied current's step average
+    const double c_up = (1.0 - ph.theta) / ph.theta;
+    const double src_scale = stim_step_scale(ph, step, dt);
     for (int a = tid; a < b.nb; a += NT) u[a] = up[a];
     cluster_barrier(cl, b.C);
     // On levels whose steps have several roots (sp.flow) the step follows the
@@ -392,10 +397,14 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
         const int A = base + a;
         auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
-        const double ku = CFAST(c) ? stencil_fast<DIM, double>(u, a, b.N0, N01, c64A)
-                                   : stencil_band<DIM, GM, double>(b, uv, CI(c), CJ(c), CK_(c), c64A);
+        double ku = CFAST(c) ? stencil_fast<DIM, double>(u, a, b.N0, N01, c64A)
+                             : stencil_band<DIM, GM, double>(b, uv, CI(c), CJ(c), CK_(c), c64A);
+        if (c_up != 0.0)
+          ku += c_up * (CFAST(c) ? stencil_fast<DIM, double>(up, a, b.N0, N01, c64A)
+                                 : stencil_band<DIM, GM, double>(b, upv, CI(c), CJ(c), CK_(c), c64A));
         const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c)), uA = u[a];
-        const double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
+        double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
+        if (src_scale != 0.0) f -= mA * src_scale * stim_shape(ph, lv, sc, CI(c), CJ(c), CK_(c));
         F[a] = f;
         // Hessian diagonal and Jacobi inverse in the CG's precision (the CG is
         // the only user); no FP64 division on the per-node path
@@ -630,8 +639,15 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
 #undef CJ
 #undef CK_
 #undef CFAST
-  for (int a = tid; a < b.nb; a += NT)
-    if (ta[base + a] < 0.0) ta[base + a] = lv.T;
+  {
+    // the quantity of interest: activation times (T where never reached), or
+    // the final state u(T) (in the buffer of step m)
+    const double* ufin = (lv.m & 1) ? ubuf1 : ubuf0;
+    for (int a = tid; a < b.nb; a += NT) {
+      if (ph.qoi == 1) ta[base + a] = ufin[a];
+      else if (ta[base + a] < 0.0) ta[base + a] = lv.T;
+    }
+  }
   if (b.rank == 0 && tid == 0) {
     if (counters) {
       if (status != MLMC_OK) atomicAdd(counters, 1ull);

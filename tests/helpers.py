@@ -10,6 +10,9 @@ from paper_1911_06066_gb300 import workloads as W
 
 def oracle_level(w, l, **kw):
     n, m = W.level_shape(w, l)
+    for key in ("scheme", "stim_kind", "stim_amp", "stim_sigma", "stim_t1", "qoi"):
+        if key in w and key not in kw:
+            kw[key] = w[key]
     return O.make_level(w["dim"], n, m, w["L"], w["T"], w["c"], w["a"], w["s_t"], w["s_l0"],
                         w["theta0"], w["theta1"], w["stim_r"], w["stim_c"], **kw)
 

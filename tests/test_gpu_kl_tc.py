@@ -85,3 +85,21 @@ def test_mixed_solve_on_the_tc_field_matches_oracle():
         so, to, _ = O.solve_sample(lv, Zo)
         amb = (np.abs(so - 0.5) < 1e-6).any(axis=0)
         assert np.abs(t[r] - to)[~amb].max() <= 1e-4 * w["T"]
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """The tensor-core kernel's bounded waits: with the check hook on, every
+    tile waits on a barrier that nothing arms (before it issues any copy or
+    MMA), gives up after a few polls and exits; the run reports
+    MLMC_ERR_TIMEOUT and the context stays usable -- with the hook off, the
+    next run equals one on a fresh context."""
+    w = dict(W.MLMC2D_3LVL, levels=2)
+    ctx = B.Context(B.make_config(w, B.MLMC_PREC_MIXED))
+    ctx.check_timeout_path(1000)
+    with pytest.raises(B.MLMCError) as e:
+        ctx.run([4, 4], seed=3, batch=4)
+    assert e.value.status == -4, str(e.value)
+    ctx.check_timeout_path(-1)
+    again = ctx.run([4, 4], seed=3, batch=4)
+    fresh = B.Context(B.make_config(w, B.MLMC_PREC_MIXED)).run([4, 4], seed=3, batch=4)
+    assert np.array_equal(again["mean"], fresh["mean"])
