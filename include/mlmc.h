@@ -114,7 +114,33 @@ typedef struct {
   double stim_sigma;     /*   stim_sigma^2) for 0 <= t < stim_t1, u(x, 0) = 0; each step  */
   double stim_t1;        /*   takes the current's exact average over the step            */
   int qoi;               /* mlmc_qoi: the nodal quantity the estimators average          */
+  /* The paper's own KL variant (Sec. 3.1.1, Eq. KL-expansion-deterministic;
+     Sec. 4): kl_kind = MLMC_KL_AFFINE_GAUSSIAN selects it; zero keeps the
+     separable exponential kernel above. */
+  int kl_kind;           /* mlmc_kl_kind                                                 */
+  double kl_tol;         /* pivoted Cholesky stops at a remainder trace <= kl_tol x trace */
+  double kl_s;           /* s of G = G0 (1 + s Z), capped by the ellipticity rule:        */
+  double kl_delta;       /*   s_eff = min(kl_s, kl_delta / max_x sum_k |l_k(x)|)         */
+  int kl_cand_level;     /* level whose cell centroids are the pivot candidates           */
 } mlmc_config;
+
+/* Random field of the conductivity.
+ * MLMC_KL_SEPARABLE_EXP: s_l = s_l0 exp(Z), Z = sum_k sqrt(lam_k) phi_k xi_k,
+ *   the analytic eigenpairs of kl_sigma2 exp(-|dx|/ell - |dy|/ell (- |dz|/ell)),
+ *   xi_k ~ N(0, 1); conductivity tensor s_t I + (s_l - s_t) f f^T.
+ * MLMC_KL_AFFINE_GAUSSIAN: the paper's G = s_l0 (1 + s_eff Z) I (isotropic),
+ *   Z = sum_k l_k(x) y_k, y_k ~ U(-1, 1) (from the same Philox words: 2u - 1),
+ *   l_k the columns of the pivoted Cholesky factor (Harbrecht, Peters &
+ *   Schneider 2012) of kl_sigma2 exp(-|x - x'|^2 / kl_ell^2) over the cell
+ *   centroids of level kl_cand_level (at most kl_modes columns, fewer when the
+ *   remainder trace falls to kl_tol of the trace), extended to every level's
+ *   centroids by the factor's own recursion (Nystrom), so that both members of
+ *   a pair see the same continuous field; s_eff keeps G within
+ *   s_l0 (1 +- kl_delta) for every y. */
+typedef enum {
+  MLMC_KL_SEPARABLE_EXP = 0,
+  MLMC_KL_AFFINE_GAUSSIAN = 1
+} mlmc_kl_kind;
 
 /* Time scheme of the space-time blocks (block row k divided by dt):
  *   F_k(u) = (M/dt)(u_k - u_{k-1}) + K (theta u_k + (1-theta) u_{k-1})
@@ -224,6 +250,10 @@ mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi, int n, dou
  * leaves its outputs unwritten and is reported by the next mlmc_run /
  * mlmc_run_more as MLMC_ERR_TIMEOUT. */
 mlmc_status mlmc_kl_tc_workspace_bytes(const mlmc_ctx* ctx, int n, size_t* bytes);
+/* The KL expansion's rank (kl_modes, or the pivoted Cholesky's rank) and, for
+ * MLMC_KL_AFFINE_GAUSSIAN, the capped scale s_eff (1 otherwise); host outputs,
+ * any may be NULL. */
+mlmc_status mlmc_kl_info(const mlmc_ctx* ctx, int* rank, double* s_eff);
 /* Check of the bounded-wait path (the paper has no counterpart): with polls >=
  * 0, every tile of the context's later tensor-core KL launches first waits at
  * most `polls` polls on a barrier that nothing arms -- before it issues any

@@ -44,7 +44,8 @@ class Level(C.Structure):
                 ("stim_c", C.c_double * 3), ("newton_tol", C.c_double),
                 ("newton_max", C.c_int), ("lin_rtol", C.c_double), ("lin_max", C.c_int),
                 ("scheme", C.c_int), ("stim_kind", C.c_int), ("stim_amp", C.c_double),
-                ("stim_sigma", C.c_double), ("stim_t1", C.c_double), ("qoi", C.c_int)]
+                ("stim_sigma", C.c_double), ("stim_t1", C.c_double), ("qoi", C.c_int),
+                ("cond_kind", C.c_int)]
 
     @property
     def nodes(self):
@@ -59,19 +60,19 @@ class Level(C.Structure):
         return self.T / self.m
 
     def shape_nodes(self):
-        if self.dim == 2:
-            return (self.n[1] + 1, self.n[0] + 1)
-        return (self.n[2] + 1, self.n[1] + 1, self.n[0] + 1)
+        return tuple(self.n[d] + 1 for d in range(self.dim))[::-1]
 
 
 def make_level(dim, n, m, L, T, c, a, s_t, s_l0, theta0, theta1=None, stim_r=0.1,
                stim_c=(0.0, 0.0, 0.0), newton_tol=1e-12, newton_max=5000,
                lin_rtol=1e-12, lin_max=5000, scheme=0, stim_kind=0, stim_amp=0.0,
-               stim_sigma=1.0, stim_t1=0.0, qoi=0):
+               stim_sigma=1.0, stim_t1=0.0, qoi=0, cond_kind=0):
     """One discretisation level.  scheme: 0 implicit Euler, 1 Crank-Nicolson
     (Sec. 3.2); stim_kind: 0 the ball u0 = 1 (radius stim_r), 1 u0 = 0 and the
     applied current stim_amp exp(-|x - stim_c|^2 / stim_sigma^2) on [0, stim_t1)
-    (Sec. 4 set-up); qoi: 0 activation time, 1 the final state u(T)."""
+    (Sec. 4 set-up); qoi: 0 activation time, 1 the final state u(T); cond_kind:
+    0 the fiber tensor with s_l = s_l0 exp(Z), 1 the paper's isotropic
+    G = s_l0 (1 + Z) (Sec. 3.1.1)."""
     lv = Level()
     lv.dim = dim
     for d in range(3):
@@ -87,6 +88,7 @@ def make_level(dim, n, m, L, T, c, a, s_t, s_l0, theta0, theta1=None, stim_r=0.1
     lv.lin_rtol, lv.lin_max = float(lin_rtol), int(lin_max)
     lv.scheme, lv.stim_kind, lv.qoi = int(scheme), int(stim_kind), int(qoi)
     lv.stim_amp, lv.stim_sigma, lv.stim_t1 = float(stim_amp), float(stim_sigma), float(stim_t1)
+    lv.cond_kind = int(cond_kind)
     return lv
 
 
@@ -98,6 +100,11 @@ def _declare(l):
     l.or_log.restype = C.c_double
     l.or_sincos_2pi.argtypes = [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     l.or_xi.argtypes = [C.c_uint64, C.c_int, C.c_uint64, C.c_int, _dp]
+    l.or_psi_uniform.argtypes = [C.c_uint64, C.c_int, C.c_uint64, C.c_int, _dp]
+    l.or_pivoted_cholesky.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double, C.c_int,
+                                      C.c_double, _ip, _dp, C.c_void_p]
+    l.or_pc_eval.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_int,
+                             _dp, _dp]
     l.or_kl_1d.argtypes = [C.c_double, C.c_double, C.c_int, _dp, _dp, _dp]
     l.or_kl_phi_1d.argtypes = [C.c_double, C.c_int, C.c_double, C.c_double, C.c_double]
     l.or_kl_phi_1d.restype = C.c_double
@@ -187,11 +194,72 @@ def kl_field(dim, L, n, sigma2, ell, M, xis):
     return Z.reshape(ns, cells)
 
 
+# ---------------------------------------------------------------- the paper's KL
+def psi_uniform(seed, level, sample_id, M):
+    """psi[0..M) ~ U(-1, 1) of sample (seed, level pair, id) (Sec. 3.1.1)."""
+    out = np.zeros(M, np.float64)
+    lib().or_psi_uniform(int(seed), int(level), int(sample_id), int(M), out)
+    return out
+
+
+def cell_centroids(dim, L, n):
+    """Cell centroids [cells][dim], x fastest."""
+    axes = [(np.arange(n[d]) + 0.5) * L[d] / n[d] for d in range(dim)]
+    grid = np.meshgrid(*axes[::-1], indexing="ij")
+    return np.ascontiguousarray(np.stack([g.ravel() for g in grid[::-1]], axis=1))
+
+
+def pivoted_cholesky(X, sigma2, ell, M, tol=0.0, want_L=False):
+    """Pivoted Cholesky of the Gaussian covariance on points X[n][dim]:
+    (rank m, pivots[m], Lpiv[M][M], L[n][M] or None)."""
+    X = np.ascontiguousarray(X, np.float64)
+    n, dim = X.shape
+    piv = np.zeros(M, np.int32)
+    Lpiv = np.zeros(M * M)
+    L = np.zeros(n * M) if want_L else None
+    m = lib().or_pivoted_cholesky(dim, n, X.ravel(), float(sigma2), float(ell), int(M), float(tol),
+                                  piv, Lpiv, None if L is None else L.ctypes.data)
+    return m, piv[:m].copy(), Lpiv.reshape(M, M), (None if L is None else L.reshape(n, M))
+
+
+def pc_eval(Y, Xp, sigma2, ell, M, m, Lpiv):
+    """The factor's columns at points Y[ny][dim] (Nystrom extension): [ny][M]."""
+    Y = np.ascontiguousarray(Y, np.float64)
+    ny, dim = Y.shape
+    Phi = np.zeros(ny * M)
+    lib().or_pc_eval(dim, ny, Y.ravel(), np.ascontiguousarray(Xp, np.float64).ravel(), float(sigma2),
+                     float(ell), int(M), int(m), np.ascontiguousarray(Lpiv, np.float64).ravel(), Phi)
+    return Phi.reshape(ny, M)
+
+
+class AffineKL:
+    """The paper's KL variant on a level hierarchy (Sec. 3.1.1 and Sec. 4):
+    Z(x, y) = sum_k l_k(x) y_k with l_k the pivoted-Cholesky columns of the
+    Gaussian covariance, pivots chosen among the cell centroids of the
+    candidate grid `cand_n`, extended to every level's centroids; G = G0 (1 +
+    s_eff Z) with s_eff = min(s, delta / max_x sum_k |l_k(x)|) over all levels'
+    centroids."""
+
+    def __init__(self, dim, L, cand_n, level_ns, sigma2, ell, M, tol, s, delta):
+        self.dim, self.L, self.M = dim, list(L), M
+        X = cell_centroids(dim, L, cand_n)
+        self.m, self.piv, self.Lpiv, _ = pivoted_cholesky(X, sigma2, ell, M, tol)
+        self.Xp = X[self.piv]
+        self.Phi = [pc_eval(cell_centroids(dim, L, n), self.Xp, sigma2, ell, M, self.m, self.Lpiv)
+                    for n in level_ns]
+        bound = max(float(np.abs(P).sum(axis=1).max()) for P in self.Phi)
+        self.s_eff = min(s, delta / bound)
+
+    def field(self, level, psi):
+        psi = np.atleast_2d(psi)
+        return self.s_eff * (psi @ self.Phi[level].T)
+
+
 # ---------------------------------------------------------------- FEM / solve
 def assemble(lv, Z):
     n = lv.nodes
     mass = np.zeros(n)
-    kst = np.zeros(n * (27 if lv.dim == 3 else 9))
+    kst = np.zeros(n * 3 ** lv.dim)
     lib().or_assemble(C.byref(lv), np.ascontiguousarray(Z, np.float64), mass, kst)
     return mass, kst
 
@@ -311,6 +379,22 @@ def sample_pair(fine, coarse, l0, sigma2, ell, M, seed, level, sample_id):
     if rc < 0:
         raise RuntimeError("oracle sample pair (level %d, id %d) failed: %d" % (level, sample_id, rc))
     return y, y2, it.value
+
+
+def sample_pair_affine(fine, coarse, l0, akl, level, seed, sample_id):
+    """(y, y2) of one level pair with the paper's KL variant: psi uniform for
+    (seed, level, id), the affine field on both grids (levels `level` and
+    `level` - 1 of `akl`), both problems solved, QoIs injected."""
+    psi = psi_uniform(seed, level, sample_id, akl.M)
+    out = []
+    for lv, l in ((fine, level), (coarse, level - 1)):
+        if lv is None:
+            out.append(np.zeros(l0.nodes))
+            continue
+        Z = akl.field(l, psi)[0]
+        _, q, _ = solve_sample(lv, Z)
+        out.append(inject(lv, l0, q))
+    return out[0] - out[1], out[0] ** 2 - out[1] ** 2
 
 
 def level_pairs(levels, l, sigma2, ell, M, seed, sample_ids, threads=1):

@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["rng.c", "kl.c", "fem.c", "solve.c", "mlmc.c"]
+SOURCES = ["rng.c", "kl.c", "kl_affine.c", "fem.c", "solve.c", "mlmc.c"]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 

@@ -17,27 +17,29 @@
 #include "oracle.h"
 
 int or_nodes(const or_level* lv) {
-  int n = (lv->n[0] + 1) * (lv->n[1] + 1);
-  if (lv->dim == 3) n *= lv->n[2] + 1;
+  int n = 1;
+  for (int d = 0; d < lv->dim; ++d) n *= lv->n[d] + 1;
   return n;
 }
 
 int or_cells(const or_level* lv) {
-  int n = lv->n[0] * lv->n[1];
-  if (lv->dim == 3) n *= lv->n[2];
+  int n = 1;
+  for (int d = 0; d < lv->dim; ++d) n *= lv->n[d];
   return n;
 }
 
-static int n_off(int dim) { return dim == 3 ? 27 : 9; }
+/* couplings per node: the 3^dim offsets in {-1,0,1}^dim, x fastest */
+int or_n_offsets(int dim) { return dim == 3 ? 27 : (dim == 2 ? 9 : 3); }
+static int n_off(int dim) { return or_n_offsets(dim); }
 
 void or_assemble(const or_level* lv, const double* Z, double* mass, double* Kst) {
   const double pi = 3.14159265358979323846;
   int dim = lv->dim;
-  int nx = lv->n[0], ny = lv->n[1], nz = dim == 3 ? lv->n[2] : 1;
-  int Nx = nx + 1, Ny = ny + 1;
+  int nx = lv->n[0], ny = dim >= 2 ? lv->n[1] : 1, nz = dim == 3 ? lv->n[2] : 1;
+  int Nx = nx + 1, Ny = dim >= 2 ? ny + 1 : 1;
   int nodes = or_nodes(lv), no = n_off(dim), nloc = 1 << dim;
-  double h[3] = {lv->L[0] / nx, lv->L[1] / ny, dim == 3 ? lv->L[2] / nz : 1.0};
-  double vol = h[0] * h[1] * (dim == 3 ? h[2] : 1.0);
+  double h[3] = {lv->L[0] / nx, dim >= 2 ? lv->L[1] / ny : 1.0, dim == 3 ? lv->L[2] / nz : 1.0};
+  double vol = h[0] * h[1] * h[2];
   memset(mass, 0, sizeof(double) * nodes);
   memset(Kst, 0, sizeof(double) * (size_t)nodes * no);
   const double gp[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
@@ -50,14 +52,20 @@ void or_assemble(const or_level* lv, const double* Z, double* mass, double* Kst)
         if (dim == 3) th = lv->theta0 + (lv->theta1 - lv->theta0) * ((kz + 0.5) * h[2]) / lv->L[2];
         th = th * pi / 180.0;
         double f[3] = {cos(th), sin(th), 0.0};
-        double sl = lv->s_l0 * exp(Z[cell]);
         double D[3][3];
-        for (int p = 0; p < 3; ++p)
-          for (int q = 0; q < 3; ++q) D[p][q] = (p == q ? lv->s_t : 0.0) + (sl - lv->s_t) * f[p] * f[q];
+        if (lv->cond_kind == 1) {   /* the paper's isotropic G = G0 (1 + Z) */
+          double g = lv->s_l0 * (1.0 + Z[cell]);
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) D[p][q] = p == q ? g : 0.0;
+        } else {
+          double sl = lv->s_l0 * exp(Z[cell]);
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) D[p][q] = (p == q ? lv->s_t : 0.0) + (sl - lv->s_t) * f[p] * f[q];
+        }
         double Ke[8][8]; double me[8];
         memset(Ke, 0, sizeof(Ke)); memset(me, 0, sizeof(me));
         for (int g = 0; g < ngauss; ++g) {
-          double xi[3] = {gp[g & 1], gp[(g >> 1) & 1], dim == 3 ? gp[(g >> 2) & 1] : 0.0};
+          double xi[3] = {gp[g & 1], dim >= 2 ? gp[(g >> 1) & 1] : 0.0, dim == 3 ? gp[(g >> 2) & 1] : 0.0};
           double w = vol / (double)ngauss; /* Gauss weights 1/2 per axis times |J| */
           double phi[8], grad[8][3];
           for (int a = 0; a < nloc; ++a) {
@@ -92,7 +100,7 @@ void or_assemble(const or_level* lv, const double* Z, double* mass, double* Kst)
           for (int b = 0; b < nloc; ++b) {
             int di = (b & 1) - (a & 1), dj = ((b >> 1) & 1) - ((a >> 1) & 1);
             int dk = ((b >> 2) & 1) - ((a >> 2) & 1);
-            int o = (di + 1) + 3 * (dj + 1) + (dim == 3 ? 9 * (dk + 1) : 0);
+            int o = (di + 1) + (dim >= 2 ? 3 * (dj + 1) : 0) + (dim == 3 ? 9 * (dk + 1) : 0);
             Kst[(size_t)A * no + o] += Ke[a][b];
           }
         }
@@ -101,7 +109,7 @@ void or_assemble(const or_level* lv, const double* Z, double* mass, double* Kst)
 
 void or_stiff_apply(const or_level* lv, const double* Kst, const double* v, double* y) {
   int dim = lv->dim;
-  int Nx = lv->n[0] + 1, Ny = lv->n[1] + 1, Nz = dim == 3 ? lv->n[2] + 1 : 1;
+  int Nx = lv->n[0] + 1, Ny = dim >= 2 ? lv->n[1] + 1 : 1, Nz = dim == 3 ? lv->n[2] + 1 : 1;
   int no = n_off(dim);
   for (int k = 0; k < Nz; ++k)
     for (int j = 0; j < Ny; ++j)
@@ -109,7 +117,7 @@ void or_stiff_apply(const or_level* lv, const double* Kst, const double* v, doub
         int A = (k * Ny + j) * Nx + i;
         double s = 0.0;
         for (int o = 0; o < no; ++o) {
-          int di = o % 3 - 1, dj = (o / 3) % 3 - 1, dk = dim == 3 ? o / 9 - 1 : 0;
+          int di = o % 3 - 1, dj = dim >= 2 ? (o / 3) % 3 - 1 : 0, dk = dim == 3 ? o / 9 - 1 : 0;
           int ii = i + di, jj = j + dj, kk = k + dk;
           if (ii < 0 || ii >= Nx || jj < 0 || jj >= Ny || kk < 0 || kk >= Nz) continue;
           s += Kst[(size_t)A * no + o] * v[(kk * Ny + jj) * Nx + ii];
@@ -125,8 +133,9 @@ void or_initial(const or_level* lv, double* u0) {
     for (int i = 0; i < n; ++i) u0[i] = 0.0;
     return;
   }
-  int Nx = lv->n[0] + 1, Ny = lv->n[1] + 1, Nz = dim == 3 ? lv->n[2] + 1 : 1;
-  double h[3] = {lv->L[0] / lv->n[0], lv->L[1] / lv->n[1], dim == 3 ? lv->L[2] / lv->n[2] : 0.0};
+  int Nx = lv->n[0] + 1, Ny = dim >= 2 ? lv->n[1] + 1 : 1, Nz = dim == 3 ? lv->n[2] + 1 : 1;
+  double h[3] = {lv->L[0] / lv->n[0], dim >= 2 ? lv->L[1] / lv->n[1] : 0.0,
+                 dim == 3 ? lv->L[2] / lv->n[2] : 0.0};
   for (int k = 0; k < Nz; ++k)
     for (int j = 0; j < Ny; ++j)
       for (int i = 0; i < Nx; ++i) {
@@ -150,8 +159,9 @@ void or_stimulus_step(const or_level* lv, int k, double* s) {
   double a = (k - 1) * dt, b = k * dt;
   double overlap = fmin(b, lv->stim_t1) - a;
   if (overlap < 0.0) overlap = 0.0;
-  int Nx = lv->n[0] + 1, Ny = lv->n[1] + 1, Nz = dim == 3 ? lv->n[2] + 1 : 1;
-  double h[3] = {lv->L[0] / lv->n[0], lv->L[1] / lv->n[1], dim == 3 ? lv->L[2] / lv->n[2] : 0.0};
+  int Nx = lv->n[0] + 1, Ny = dim >= 2 ? lv->n[1] + 1 : 1, Nz = dim == 3 ? lv->n[2] + 1 : 1;
+  double h[3] = {lv->L[0] / lv->n[0], dim >= 2 ? lv->L[1] / lv->n[1] : 0.0,
+                 dim == 3 ? lv->L[2] / lv->n[2] : 0.0};
   for (int kk = 0; kk < Nz; ++kk)
     for (int j = 0; j < Ny; ++j)
       for (int i = 0; i < Nx; ++i) {

@@ -13,8 +13,8 @@
 void or_inject(const or_level* fine, const or_level* l0, const double* f, double* out) {
   int dim = fine->dim;
   int r = fine->n[0] / l0->n[0];
-  int Nxf = fine->n[0] + 1, Nyf = fine->n[1] + 1;
-  int Nx0 = l0->n[0] + 1, Ny0 = l0->n[1] + 1, Nz0 = dim == 3 ? l0->n[2] + 1 : 1;
+  int Nxf = fine->n[0] + 1, Nyf = dim >= 2 ? fine->n[1] + 1 : 1;
+  int Nx0 = l0->n[0] + 1, Ny0 = dim >= 2 ? l0->n[1] + 1 : 1, Nz0 = dim == 3 ? l0->n[2] + 1 : 1;
   for (int k = 0; k < Nz0; ++k)
     for (int j = 0; j < Ny0; ++j)
       for (int i = 0; i < Nx0; ++i)

@@ -22,6 +22,9 @@ void or_sincos_2pi(double u, double* s, double* c); /* sin/cos of 2*pi*u      */
 /* xi[0..M) for (seed, level pair, sample id): standard normals, Box-Muller.   */
 void or_xi(uint64_t seed, int level, uint64_t sample_id, int M, double* xi);
 
+/* psi[0..M) ~ U(-1, 1) for (seed, level pair, sample id), the same counters. */
+void or_psi_uniform(uint64_t seed, int level, uint64_t sample_id, int M, double* psi);
+
 /* ---------- Karhunen-Loeve expansion (Sec. 3.1.1, Eq. KL-expansion) ---------- */
 /* 1D eigenpairs of exp(-|x-y|/ell) on an interval of length len, modes 0..n-1
  * (decreasing eigenvalue).  omega[n], lam[n] (unit variance), nrm[n] = the
@@ -38,9 +41,21 @@ int or_kl_table(int dim, const double* L, double sigma2, double ell, int M,
 int or_kl_field(int dim, const double* L, const int* n, double sigma2, double ell,
                 int M, int nsamp, const double* xi, double* Z);
 
+/* The paper's KL variant (kl_affine.c): pivoted Cholesky of the Gaussian
+ * covariance sigma2 exp(-|x-x'|^2/ell^2) on n candidate points X[n][dim], at
+ * most M columns, stopped at a remainder trace <= tol times the full trace.
+ * piv[M] pivot indices, Lpiv[M][M] the pivot rows of the factor (lower
+ * triangular), L[n][M] (may be NULL) the factor.  Returns the rank m. */
+int or_pivoted_cholesky(int dim, int n, const double* X, double sigma2, double ell, int M,
+                        double tol, int* piv, double* Lpiv, double* L);
+/* The factor's columns at any points Y[ny][dim] (Nystrom extension from the
+ * pivot points Xp[m][dim] and Lpiv): Phi[ny][M] (columns >= m zero). */
+void or_pc_eval(int dim, int ny, const double* Y, const double* Xp, double sigma2, double ell,
+                int M, int m, const double* Lpiv, double* Phi);
+
 /* ---------- one discretisation level --------------------------------------- */
 typedef struct {
-  int dim;            /* 2 or 3                                                */
+  int dim;            /* 1, 2 or 3                                             */
   int n[3];           /* cells per axis (n[2] ignored in 2D)                    */
   int m;              /* implicit-Euler steps                                   */
   double L[3];        /* domain extents                                         */
@@ -61,10 +76,13 @@ typedef struct {
                          for 0 <= t < stim_t1 (Sec. 4 set-up)                    */
   double stim_amp, stim_sigma, stim_t1;
   int qoi;            /* 0: activation time; 1: the final state u(T)            */
+  int cond_kind;      /* 0: D = s_t I + (s_l0 e^Z - s_t) f f^T (fiber, lognormal);
+                         1: D = s_l0 (1 + Z) I (the paper's affine isotropic G)  */
 } or_level;
 
 int or_nodes(const or_level* lv);
 int or_cells(const or_level* lv);
+int or_n_offsets(int dim);   /* 3^dim */
 /* Lumped mass (row sums of the Q1 consistent mass), stiffness stored per node
  * as 3^dim couplings to offsets in {-1,0,1}^dim (x fastest). */
 void or_assemble(const or_level* lv, const double* Z, double* mass, double* Kst);

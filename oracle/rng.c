@@ -105,3 +105,21 @@ void or_xi(uint64_t seed, int level, uint64_t sample_id, int M, double* xi) {
     if (2 * j + 1 < M) xi[2 * j + 1] = r * sn;
   }
 }
+
+/* The paper's uniform KL inputs psi_k ~ U(-1, 1) (Sec. 3.1.1) from the same
+ * Philox words as or_xi: psi_2j = 2 u1 - 1 in (-1, 1], psi_2j+1 = 2 u2 - 1 in
+ * [-1, 1), exact in binary arithmetic. */
+void or_psi_uniform(uint64_t seed, int level, uint64_t sample_id, int M, double* psi) {
+  const double two_m52 = 1.0 / 4503599627370496.0;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int j = 0; 2 * j < M; ++j) {
+    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)sample_id, (uint32_t)(sample_id >> 32),
+                       (uint32_t)level};
+    uint32_t w[4];
+    or_philox4x32_10(ctr, key, w);
+    uint64_t k1 = ((uint64_t)(w[0] >> 5) << 26) | (uint64_t)(w[1] >> 6);
+    uint64_t k2 = ((uint64_t)(w[2] >> 5) << 26) | (uint64_t)(w[3] >> 6);
+    psi[2 * j] = (double)(k1 + 1) * two_m52 - 1.0;
+    if (2 * j + 1 < M) psi[2 * j + 1] = (double)k2 * two_m52 - 1.0;
+  }
+}

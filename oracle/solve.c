@@ -106,7 +106,7 @@ static double dot(int n, const double* a, const double* b) {
 static int shifted_cg(int n, const double* mass, const double* Kst, const or_level* lv,
                       const double* u_lin, double shift, const double* F, double* d,
                       int* truncated) {
-  int no = lv->dim == 3 ? 27 : 9, ctr = lv->dim == 3 ? 13 : 4;
+  int no = or_n_offsets(lv->dim), ctr = (no - 1) / 2;
   double dt = lv->T / lv->m;
   double* pinv = malloc(sizeof(double) * n);
   double* r = malloc(sizeof(double) * n);
@@ -285,7 +285,7 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
  */
 static int prox_cg(int n, const double* mass, const double* Kst, const or_level* lv,
                    const double* w, double inv_tau, const double* G, double* d) {
-  int no = lv->dim == 3 ? 27 : 9, ctr = lv->dim == 3 ? 13 : 4;
+  int no = or_n_offsets(lv->dim), ctr = (no - 1) / 2;
   double dt = lv->T / lv->m;
   double* pinv = malloc(sizeof(double) * n);
   double* r = malloc(sizeof(double) * n);
@@ -420,7 +420,7 @@ void or_activation(int nodes, int m, double dt, double T, const double* slab, do
 
 int or_solve_sample(const or_level* lv, const double* Z, const double* u0, double* slab,
                     double* t_act, int* newton_per_step) {
-  int n = or_nodes(lv), no = lv->dim == 3 ? 27 : 9;
+  int n = or_nodes(lv), no = or_n_offsets(lv->dim);
   double* mass = malloc(sizeof(double) * n);
   double* Kst = malloc(sizeof(double) * (size_t)n * no);
   or_assemble(lv, Z, mass, Kst);

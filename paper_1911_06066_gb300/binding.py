@@ -34,7 +34,9 @@ class mlmc_config(C.Structure):
                 ("mixed_cdr_max", C.c_double), ("cluster_size", C.c_int), ("precond", C.c_int),
                 ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int), ("use_graph", C.c_int),
                 ("time_scheme", C.c_int), ("stim_kind", C.c_int), ("stim_amp", C.c_double),
-                ("stim_sigma", C.c_double), ("stim_t1", C.c_double), ("qoi", C.c_int)]
+                ("stim_sigma", C.c_double), ("stim_t1", C.c_double), ("qoi", C.c_int),
+                ("kl_kind", C.c_int), ("kl_tol", C.c_double), ("kl_s", C.c_double),
+                ("kl_delta", C.c_double), ("kl_cand_level", C.c_int)]
 
 
 MLMC_SOLVER_AUTO, MLMC_SOLVER_BLOCK, MLMC_SOLVER_CLUSTER = 0, 1, 2
@@ -42,6 +44,7 @@ MLMC_PRECOND_JACOBI, MLMC_PRECOND_GMG = 0, 1
 MLMC_SCHEME_IE, MLMC_SCHEME_CN = 0, 1
 MLMC_STIM_BALL, MLMC_STIM_PULSE = 0, 1
 MLMC_QOI_ACTIVATION, MLMC_QOI_FINAL_STATE = 0, 1
+MLMC_KL_SEPARABLE_EXP, MLMC_KL_AFFINE_GAUSSIAN = 0, 1
 
 
 class mlmc_sample_info(C.Structure):
@@ -112,6 +115,7 @@ def lib():
             "mlmc_diagnostics": ([vp, vp, vp, vp, vp], ip),
             "mlmc_level_stats": ([vp, vp], ip),
             "mlmc_check_timeout_path": ([vp, C.c_longlong], ip),
+            "mlmc_kl_info": ([vp, C.POINTER(ip), C.POINTER(C.c_double)], ip),
             "mlmc_get_state": ([vp, vp, vp, vp, vp, vp], ip),
             "mlmc_set_state": ([vp, vp, vp, vp, vp, vp], ip),
             "mlmc_merge_states": ([ip, i64, vp, vp, vp, vp, vp, vp, vp, vp], ip),
@@ -146,7 +150,7 @@ def exported_symbols():
             "mlmc_slab_residual",
             "mlmc_activation", "mlmc_sample_level", "mlmc_accumulate", "mlmc_reset",
             "mlmc_estimate", "mlmc_run", "mlmc_run_workspace_bytes", "mlmc_run_more",
-            "mlmc_run_to_rmse", "mlmc_diagnostics", "mlmc_level_stats", "mlmc_check_timeout_path", "mlmc_get_state", "mlmc_set_state", "mlmc_merge_states",
+            "mlmc_run_to_rmse", "mlmc_diagnostics", "mlmc_level_stats", "mlmc_check_timeout_path", "mlmc_kl_info", "mlmc_get_state", "mlmc_set_state", "mlmc_merge_states",
             "mlmc_autotune", "mlmc_get_layout", "mlmc_set_layout", "mlmc_server_create",
             "mlmc_server_submit", "mlmc_server_poll", "mlmc_server_drain", "mlmc_server_stats",
             "mlmc_server_clock", "mlmc_server_estimate", "mlmc_server_error",
@@ -253,6 +257,13 @@ def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, 
     c.stim_sigma = float(w.get("stim_sigma", 1.0))
     c.stim_t1 = float(w.get("stim_t1", 0.0))
     c.qoi = int(w.get("qoi", MLMC_QOI_ACTIVATION))
+    # the paper's KL variant (workload keys kl_kind / kl_tol / kl_s / kl_delta /
+    # kl_cand_level; sigma2 and ell then describe the Gaussian covariance)
+    c.kl_kind = int(w.get("kl_kind", MLMC_KL_SEPARABLE_EXP))
+    c.kl_tol = float(w.get("kl_tol", 0.0))
+    c.kl_s = float(w.get("kl_s", 0.3))
+    c.kl_delta = float(w.get("kl_delta", 0.5))
+    c.kl_cand_level = int(w.get("kl_cand_level", 0))
     return c
 
 
@@ -476,6 +487,12 @@ class Context:
         return dict(N_l=N, mean=mean, var=var, V_l=V, C_l=Cl, rmse=rmse.value, bias=bias.value,
                     reached=st == MLMC_OK,
                     message=lib().mlmc_last_error(self.h).decode() if st != MLMC_OK else "")
+
+    def kl_info(self):
+        """(rank of the KL expansion, s_eff) (mlmc_kl_info)."""
+        r, sv = C.c_int(), C.c_double()
+        self._check(lib().mlmc_kl_info(self.h, C.byref(r), C.byref(sv)))
+        return r.value, sv.value
 
     def check_timeout_path(self, polls):
         """polls >= 0: the tensor-core KL tiles time out on purpose (before

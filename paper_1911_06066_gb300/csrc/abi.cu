@@ -171,6 +171,7 @@ void mlmc::derive_physics(const mlmc_config& c, Physics* out) {
   ph.stim_isig2 = c.stim_kind == MLMC_STIM_PULSE ? 1.0 / (c.stim_sigma * c.stim_sigma) : 0.0;
   ph.stim_t1 = c.stim_t1;
   ph.qoi = c.qoi;
+  ph.cond_kind = c.kl_kind == MLMC_KL_AFFINE_GAUSSIAN ? 1 : 0;
   *out = ph;
 }
 
@@ -220,6 +221,12 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   if (c.mg_nu < 0 || c.mg_nu > 8 || c.mg_coarse_sweeps < 0 || c.mg_coarse_sweeps > 64)
     return fail(nullptr, MLMC_ERR_ARG, "mg_nu must be 0..8 and mg_coarse_sweeps 0..64");
   if (!model_config_ok(c)) return fail(nullptr, MLMC_ERR_ARG, "time scheme, stimulus or QoI out of range");
+  if (c.kl_kind != MLMC_KL_SEPARABLE_EXP && c.kl_kind != MLMC_KL_AFFINE_GAUSSIAN)
+    return fail(nullptr, MLMC_ERR_ARG, "unknown KL kind");
+  if (c.kl_kind == MLMC_KL_AFFINE_GAUSSIAN &&
+      (!(c.kl_tol >= 0.0) || !(c.kl_s >= 0.0) || !(c.kl_delta > 0.0 && c.kl_delta < 1.0) ||
+       c.kl_cand_level < 0 || c.kl_cand_level >= c.n_levels))
+    return fail(nullptr, MLMC_ERR_ARG, "affine KL parameters out of range");
 
   mlmc_ctx* ctx = new mlmc_ctx();
   ctx->cfg = c;
@@ -237,7 +244,11 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   ctx->M = c.kl_modes;
   std::vector<int> idx;
   std::vector<double> sl;
-  if (!kl_table_host(c.dim, c.L, c.kl_sigma2, c.kl_ell, c.kl_modes, idx, sl)) {
+  const bool affine = c.kl_kind == MLMC_KL_AFFINE_GAUSSIAN;
+  if (affine) {
+    idx.assign(3 * c.kl_modes, 0);       // unused: the modes come from the factor
+    sl.assign(c.kl_modes, 0.0);          // filled with s_eff below
+  } else if (!kl_table_host(c.dim, c.L, c.kl_sigma2, c.kl_ell, c.kl_modes, idx, sl)) {
     delete ctx;
     return fail(nullptr, MLMC_ERR_ARG, "KL mode table could not be built");
   }
@@ -251,9 +262,43 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   };
   if ((e = cudaMalloc(&ctx->d_sqrt_lam, sizeof(double) * c.kl_modes)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
   if ((e = cudaMalloc(&ctx->d_idx, sizeof(int) * 3 * c.kl_modes)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+  if (affine) {
+    // the paper's KL: pivoted Cholesky on the candidate level's centroids,
+    // the mode tables of every level, s_eff = min(s, delta / max sum |l_k|)
+    LevelDesc cand;
+    std::string why;
+    if (!derive_level(c, c.kl_cand_level, &cand, &why)) { mlmc_destroy(ctx); return fail(nullptr, MLMC_ERR_ARG, why); }
+    std::vector<double> xp, lpiv;
+    ctx->kl_rank = pivoted_cholesky_host(c.dim, c.L, cand.n, c.kl_sigma2, c.kl_ell, c.kl_modes,
+                                         c.kl_tol, xp, lpiv);
+    if (ctx->kl_rank < 1) { mlmc_destroy(ctx); return fail(nullptr, MLMC_ERR_ARG, "KL factor has rank 0"); }
+    unsigned long long* d_bound = nullptr;
+    if ((e = cudaMalloc(&ctx->d_xp, sizeof(double) * xp.size())) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&ctx->d_lpiv, sizeof(double) * lpiv.size())) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&d_bound, sizeof(unsigned long long))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+    if ((e = cudaMemcpy(ctx->d_xp, xp.data(), sizeof(double) * xp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
+    if ((e = cudaMemcpy(ctx->d_lpiv, lpiv.data(), sizeof(double) * lpiv.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
+    if ((e = cudaMemset(d_bound, 0, sizeof(unsigned long long))) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
+    for (int l = 0; l < c.n_levels; ++l) {
+      const size_t cnt = (size_t)ctx->lv[l].cells * c.kl_modes;
+      if ((e = cudaMalloc(&ctx->d_tab64[l], sizeof(double) * cnt)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+      if ((e = cudaMalloc(&ctx->d_tab32[l], sizeof(float) * cnt)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
+      if ((e = launch_pc_eval(ctx->lv[l], c.kl_modes, ctx->kl_rank, c.kl_sigma2, c.kl_ell, ctx->d_xp,
+                              ctx->d_lpiv, ctx->d_tab64[l], ctx->d_tab32[l], d_bound, nullptr)) != cudaSuccess)
+        return cleanup_fail(e, "pc_eval");
+    }
+    unsigned long long bits = 0;
+    e = cudaMemcpy(&bits, d_bound, sizeof bits, cudaMemcpyDeviceToHost);
+    cudaFree(d_bound);
+    if (e != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
+    double bound;
+    memcpy(&bound, &bits, sizeof bound);
+    ctx->kl_s_eff = bound > 0.0 ? fmin(c.kl_s, c.kl_delta / bound) : c.kl_s;
+    for (int q = 0; q < c.kl_modes; ++q) sl[q] = ctx->kl_s_eff;
+  }
   if ((e = cudaMemcpy(ctx->d_sqrt_lam, sl.data(), sizeof(double) * c.kl_modes, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
   if ((e = cudaMemcpy(ctx->d_idx, idx.data(), sizeof(int) * 3 * c.kl_modes, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
-  for (int l = 0; l < c.n_levels; ++l)
+  for (int l = 0; l < c.n_levels && !affine; ++l)
     for (int d = 0; d < c.dim; ++d) {
       std::vector<double> tab;
       kl_phi_table_host(c.L[d], c.kl_ell, n1d[d], ctx->lv[l].n[d], tab);
@@ -291,6 +336,12 @@ extern "C" void mlmc_destroy(mlmc_ctx* ctx) {
       cudaFree(ctx->d_phi[l][d]);
       cudaFree(ctx->d_phi32[l][d]);
     }
+  for (int l = 0; l < MLMC_MAX_LEVELS; ++l) {
+    cudaFree(ctx->d_tab64[l]);
+    cudaFree(ctx->d_tab32[l]);
+  }
+  cudaFree(ctx->d_xp);
+  cudaFree(ctx->d_lpiv);
   cudaFree(ctx->d_acc);
   cudaFree(ctx->d_N);
   cudaFree(ctx->d_est);
@@ -354,7 +405,7 @@ extern "C" mlmc_status mlmc_xi(mlmc_ctx* ctx, uint64_t seed, int level, const ui
   if (!ctx) return MLMC_ERR_ARG;
   if (n < 0 || (n > 0 && (!ids || !xi))) return fail(ctx, MLMC_ERR_ARG, "mlmc_xi: bad arguments");
   if (level < 0) return fail(ctx, MLMC_ERR_ARG, "mlmc_xi: negative level");
-  CK(ctx, launch_xi(seed, nullptr, level, ids, n, ctx->M, xi, (cudaStream_t)stream));
+  CK(ctx, launch_xi(seed, nullptr, level, ids, n, ctx->M, ctx->cfg.kl_kind, xi, (cudaStream_t)stream));
   return MLMC_OK;
 }
 
@@ -363,9 +414,13 @@ extern "C" mlmc_status mlmc_kl_field(mlmc_ctx* ctx, int level, const double* xi,
   if (!ctx) return MLMC_ERR_ARG;
   if (bad_level(ctx, level)) return MLMC_ERR_ARG;
   if (n < 0 || (n > 0 && (!xi || !Z))) return fail(ctx, MLMC_ERR_ARG, "mlmc_kl_field: bad arguments");
-  CK(ctx, launch_kl_field(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_idx, ctx->d_phi[level][0],
-                          ctx->d_phi[level][1], ctx->d_phi[level][2], 0, xi, n, Z,
-                          (cudaStream_t)stream));
+  if (ctx->cfg.kl_kind == MLMC_KL_AFFINE_GAUSSIAN)
+    CK(ctx, launch_kl_field_table(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_tab64[level], xi, n,
+                                  Z, (cudaStream_t)stream));
+  else
+    CK(ctx, launch_kl_field(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_idx, ctx->d_phi[level][0],
+                            ctx->d_phi[level][1], ctx->d_phi[level][2], 0, xi, n, Z,
+                            (cudaStream_t)stream));
   ctx->launches += 1;
   return MLMC_OK;
 }
@@ -386,7 +441,8 @@ extern "C" mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* 
   if (!check_ws(ctx, ws, ws_bytes, kl_tc_workspace_bytes(ctx->M, n))) return MLMC_ERR_WORKSPACE;
   CK(ctx, launch_kl_field_tc(ctx->lv[level], ctx->M, ctx->d_sqrt_lam, ctx->d_idx,
                              ctx->d_phi32[level][0], ctx->d_phi32[level][1],
-                             ctx->d_phi32[level][2], xi, n, Z, ws, ctx->d_cnt + CNT_TC_TIMEOUT,
+                             ctx->d_phi32[level][2], ctx->d_tab32[level], xi, n, Z, ws,
+                             ctx->d_cnt + CNT_TC_TIMEOUT,
                              ctx->tc_check_limit, (cudaStream_t)stream));
   ctx->launches += 2;
   return MLMC_OK;
@@ -515,7 +571,7 @@ extern "C" mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, co
   double* Z = (double*)(p + w.Zf);
   double* t = (double*)(p + w.tf);
   mlmc_sample_info* inf = (mlmc_sample_info*)(p + w.info);
-  CK(ctx, launch_xi(seed, nullptr, level, ids, n, ctx->M, xi, st));
+  CK(ctx, launch_xi(seed, nullptr, level, ids, n, ctx->M, ctx->cfg.kl_kind, xi, st));
   mlmc_status r;
   if ((r = mlmc_kl_field(ctx, level, xi, n, Z, st)) != MLMC_OK) return r;
   // candidates: the block kernel (only when the layout is not forced), shared-
@@ -625,7 +681,7 @@ mlmc_status mlmc::sample_level_into(mlmc_ctx* ctx, int level, uint64_t seed, con
   double* Zf = (double*)(ws + w.Zf);
   double* tf = t_fine ? t_fine : (double*)(ws + w.tf);
   mlmc_sample_info* inf = info ? info : (mlmc_sample_info*)(ws + w.info);
-  CK(ctx, launch_xi(seed, seeds, level, ids, n, ctx->M, xi, st_f));
+  CK(ctx, launch_xi(seed, seeds, level, ids, n, ctx->M, ctx->cfg.kl_kind, xi, st_f));
   ctx->launches += 1;
   mlmc_status r;
   if ((r = kl_into(ctx, level, xi, n, Zf, ws + w.kl, st_f)) != MLMC_OK) return r;
@@ -891,6 +947,13 @@ static mlmc_status fill_stats(mlmc_ctx* ctx, double* stats) {
     snprintf(b, sizeof b, "%llu sample solves did not converge", tot[0]);
     return fail(ctx, MLMC_ERR_NOT_CONVERGED, b);
   }
+  return MLMC_OK;
+}
+
+extern "C" mlmc_status mlmc_kl_info(const mlmc_ctx* ctx, int* rank, double* s_eff) {
+  if (!ctx) return MLMC_ERR_ARG;
+  if (rank) *rank = ctx->cfg.kl_kind == MLMC_KL_AFFINE_GAUSSIAN ? ctx->kl_rank : ctx->M;
+  if (s_eff) *s_eff = ctx->cfg.kl_kind == MLMC_KL_AFFINE_GAUSSIAN ? ctx->kl_s_eff : 1.0;
   return MLMC_OK;
 }
 

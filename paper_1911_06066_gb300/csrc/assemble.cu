@@ -67,10 +67,16 @@ __global__ void assemble_kernel(LevelDesc lv, Physics ph, const double* __restri
         double th = ph.th0;
         if (DIM == 3) th = ph.th0 + (ph.th1 - ph.th0) * ((cell[2] + 0.5) * lv.h[2]) / ph.Lz;
         double f[3] = {cos(th), sin(th), 0.0};
-        double sl = ph.s_l0 * exp(Zs[ci]);
         double D[3][3];
-        for (int p = 0; p < 3; ++p)
-          for (int q = 0; q < 3; ++q) D[p][q] = (p == q ? ph.s_t : 0.0) + (sl - ph.s_t) * f[p] * f[q];
+        if (ph.cond_kind == 1) {   // the paper's isotropic G = G0 (1 + Z)
+          const double g = ph.s_l0 * (1.0 + Zs[ci]);
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) D[p][q] = p == q ? g : 0.0;
+        } else {
+          const double sl = ph.s_l0 * exp(Zs[ci]);
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) D[p][q] = (p == q ? ph.s_t : 0.0) + (sl - ph.s_t) * f[p] * f[q];
+        }
         int a[3] = {-cx, -cy, -cz};
         for (int bz = 0; bz < (DIM == 3 ? 2 : 1); ++bz)
           for (int by = 0; by < 2; ++by)

@@ -17,6 +17,14 @@ struct mlmc_ctx {
   int* d_idx = nullptr;
   double* d_phi[MLMC_MAX_LEVELS][3] = {};
   float* d_phi32[MLMC_MAX_LEVELS][3] = {};   // FP32 copies (tensor-core KL synthesis)
+  // the paper's KL variant (kl_kind 1): per level the mode table [cells][M]
+  // (FP64 and FP32), the pivots and pivot rows of the factor, the rank, s_eff
+  double* d_tab64[MLMC_MAX_LEVELS] = {};
+  float* d_tab32[MLMC_MAX_LEVELS] = {};
+  double* d_xp = nullptr;
+  double* d_lpiv = nullptr;
+  int kl_rank = 0;
+  double kl_s_eff = 0.0;
   double* d_acc = nullptr;        // [3][levels][nodes0]: mean, M2, mean of Y2
   int64_t* d_N = nullptr;         // [levels]
   double* d_est = nullptr;        // estimate output

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "mlmc.h"
 
@@ -42,6 +43,7 @@ struct Physics {
   int stim_kind;
   double stim_amp, stim_isig2, stim_t1;
   int qoi;               // 0: activation time; 1: the final state u(T)
+  int cond_kind;         // 0: fiber tensor, s_l = s_l0 exp(Z); 1: isotropic s_l0 (1 + Z)
 };
 
 // The applied current averaged over step k (1-based) at squared distance r2
@@ -173,7 +175,25 @@ __device__ inline double rxn_d(const Physics& p, double u) {
 
 // Kernels and launchers (defined in the .cu files).
 cudaError_t launch_xi(uint64_t seed, const uint64_t* seeds, int level, const uint64_t* ids, int n,
-                      int M, double* xi, cudaStream_t st);
+                      int M, int uniform, double* xi, cudaStream_t st);
+// The paper's KL variant (kl_affine.cu).  Host: pivoted Cholesky of the
+// Gaussian covariance sigma2 exp(-|x - x'|^2 / ell^2) on the cell centroids of
+// an n[3] grid (at most M columns; stop at a remainder trace <= tol of the
+// full trace): the pivot coordinates xp [m][3] and the pivot rows of the
+// factor lpiv [M][M]; returns the rank m.
+int pivoted_cholesky_host(int dim, const double* L, const int* n, double sigma2, double ell, int M,
+                          double tol, std::vector<double>& xp, std::vector<double>& lpiv);
+// Device: the factor's columns at the cell centroids of lv (Nystrom
+// extension), phi64 [cells][M] and phi32 (same in FP32, may be NULL); and the
+// largest sum_k |phi_k| over the cells into *bound (device, atomic max on the
+// bits of a non-negative double; zero it first).
+cudaError_t launch_pc_eval(const LevelDesc& lv, int M, int m, double sigma2, double ell,
+                           const double* xp, const double* lpiv, double* phi64, float* phi32,
+                           unsigned long long* bound, cudaStream_t st);
+// Z[s][cell] = sum_k phi64[cell][k] coef[k] xi[s][k] (FP64), the affine field.
+cudaError_t launch_kl_field_table(const LevelDesc& lv, int M, const double* coef,
+                                  const double* phi64, const double* xi, int n, double* Z,
+                                  cudaStream_t st);
 cudaError_t launch_kl_field(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
                             const double* phi_x, const double* phi_y, const double* phi_z,
                             int n1d, const double* xi, int n, double* Z, cudaStream_t st);
@@ -186,9 +206,11 @@ cudaError_t launch_kl_field(const LevelDesc& lv, int M, const double* sqrt_lam, 
 // barrier nothing arms, before issuing any copy or MMA, and takes its timeout
 // exit; -1 for normal operation.
 size_t kl_tc_workspace_bytes(int M, int n);
+// phi_cells (FP32 [cells][M], or NULL): an explicit mode table instead of the
+// separable 1D tables (the paper's KL variant).
 cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
                                const float* phi_x, const float* phi_y, const float* phi_z,
-                               const double* xi, int n, double* Z, void* ws,
+                               const float* phi_cells, const double* xi, int n, double* Z, void* ws,
                                unsigned long long* err, long long check_limit, cudaStream_t st);
 cudaError_t preload_kl_tc();
 cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,

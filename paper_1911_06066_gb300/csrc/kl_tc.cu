@@ -22,7 +22,9 @@
 // shape 128 x NT x 8 into the TMEM accumulator and commits them to the
 // stage's 'done' mbarrier, which the threads wait on before they refill that
 // stage two chunks later -- so staging of chunk c+1 overlaps the MMAs of
-// chunk c.  The epilogue reads the accumulator with tcgen05.ld (warps w and
+// chunk c.  (With an explicit FP32 mode table -- the paper's KL variant --
+// the A operand is read from it instead of the separable 1D tables.)  The
+// epilogue reads the accumulator with tcgen05.ld (warps w and
 // w+4 read TMEM lanes 32(w%4).. = the tile's cells, half the columns each)
 // and writes Z in FP64, coalesced along the cells.
 //
@@ -184,8 +186,9 @@ __global__ void kl_tc_prep_kernel(int M, int n, int nt, int chunks, const double
 __global__ void __launch_bounds__(TC_THREADS)
 kl_field_tc_kernel(LevelDesc lv, int M, int nt, const int* __restrict__ idx,
                    const float* __restrict__ phx, const float* __restrict__ phy,
-                   const float* __restrict__ phz, const unsigned char* __restrict__ bprep, int n,
-                   double* __restrict__ Z, unsigned long long* err, long long check_limit) {
+                   const float* __restrict__ phz, const float* __restrict__ phi_cells,
+                   const unsigned char* __restrict__ bprep, int n, double* __restrict__ Z,
+                   unsigned long long* err, long long check_limit) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   // align the operand tiles to 1024 bytes (the swizzle atom)
   unsigned char* sm = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
@@ -270,9 +273,13 @@ kl_field_tc_kernel(LevelDesc lv, int M, int nt, const int* __restrict__ idx,
       const int mode = c * TC_KC + k;
       float v = 0.f;
       if (avalid && mode < M) {
-        v = phx[(int64_t)idx[3 * mode] * lv.n[0] + ai];
-        if (lv.dim >= 2) v *= phy[(int64_t)idx[3 * mode + 1] * lv.n[1] + aj];
-        if (lv.dim >= 3) v *= phz[(int64_t)idx[3 * mode + 2] * lv.n[2] + ak];
+        if (phi_cells) {
+          v = phi_cells[acell * M + mode];    // explicit mode table (the paper's KL)
+        } else {
+          v = phx[(int64_t)idx[3 * mode] * lv.n[0] + ai];
+          if (lv.dim >= 2) v *= phy[(int64_t)idx[3 * mode + 1] * lv.n[1] + aj];
+          if (lv.dim >= 3) v *= phz[(int64_t)idx[3 * mode + 2] * lv.n[2] + ak];
+        }
       }
       const float h = tf32_hi(v);
       *(float*)(sm + L.a_hi[st] + sw128(arow, k)) = h;
@@ -373,7 +380,7 @@ cudaError_t preload_kl_tc() {
 
 cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_lam, const int* idx,
                                const float* phi_x, const float* phi_y, const float* phi_z,
-                               const double* xi, int n, double* Z, void* ws,
+                               const float* phi_cells, const double* xi, int n, double* Z, void* ws,
                                unsigned long long* err, long long check_limit, cudaStream_t st) {
   if (n == 0 || lv.cells == 0) return cudaSuccess;
   const int nt = kl_tc_nt(n);
@@ -387,7 +394,7 @@ cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_la
   const int64_t mt = (lv.cells + TC_M - 1) / TC_M;
   if (mt > 0x7fffffff || tiles > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)mt, (unsigned)tiles);
-  kl_field_tc_kernel<<<grid, TC_THREADS, smem, st>>>(lv, M, nt, idx, phi_x, phi_y, phi_z,
+  kl_field_tc_kernel<<<grid, TC_THREADS, smem, st>>>(lv, M, nt, idx, phi_x, phi_y, phi_z, phi_cells,
                                                      (const unsigned char*)ws, n, Z, err,
                                                      check_limit);
   return cudaGetLastError();

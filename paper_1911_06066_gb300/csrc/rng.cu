@@ -87,8 +87,11 @@ __device__ void sincos_2pi_series(double u, double* s_out, double* c_out) {
 }
 
 // One thread per (sample, mode pair).
+// uniform != 0: the paper's psi ~ U(-1, 1) from the same words instead of
+// normals, psi_2j = 2 u1 - 1, psi_2j+1 = 2 u2 - 1 (exact in binary).
 __global__ void xi_kernel(uint64_t seed0, const uint64_t* __restrict__ seeds, int level,
-                          const uint64_t* __restrict__ ids, int n, int M, double* __restrict__ xi) {
+                          const uint64_t* __restrict__ ids, int n, int M, int uniform,
+                          double* __restrict__ xi) {
   int pairs = (M + 1) / 2;
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)n * pairs) return;
@@ -101,6 +104,13 @@ __global__ void xi_kernel(uint64_t seed0, const uint64_t* __restrict__ seeds, in
   const double two_m53 = 1.1102230246251565404e-16;  // 2^-53, exact
   unsigned long long k1 = ((unsigned long long)(w[0] >> 5) << 26) | (unsigned long long)(w[1] >> 6);
   unsigned long long k2 = ((unsigned long long)(w[2] >> 5) << 26) | (unsigned long long)(w[3] >> 6);
+  if (uniform) {
+    const double two_m52 = 2.220446049250313080847e-16;  // 2^-52, exact
+    xi[(int64_t)s * M + 2 * j] = __dadd_rn(__dmul_rn(__ull2double_rn(k1 + 1ull), two_m52), -1.0);
+    if (2 * j + 1 < M)
+      xi[(int64_t)s * M + 2 * j + 1] = __dadd_rn(__dmul_rn(__ull2double_rn(k2), two_m52), -1.0);
+    return;
+  }
   double u1 = __dmul_rn(__ull2double_rn(k1 + 1ull), two_m53);
   double u2 = __dmul_rn(__ull2double_rn(k2), two_m53);
   double r = __dsqrt_rn(__dmul_rn(-2.0, ln_series(u1)));
@@ -111,11 +121,12 @@ __global__ void xi_kernel(uint64_t seed0, const uint64_t* __restrict__ seeds, in
 }
 
 cudaError_t launch_xi(uint64_t seed, const uint64_t* seeds, int level, const uint64_t* ids, int n,
-                      int M, double* xi, cudaStream_t st) {
+                      int M, int uniform, double* xi, cudaStream_t st) {
   int64_t total = (int64_t)n * ((M + 1) / 2);
   if (total == 0) return cudaSuccess;
   int bs = 128;
-  xi_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(seed, seeds, level, ids, n, M, xi);
+  xi_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(seed, seeds, level, ids, n, M, uniform,
+                                                               xi);
   return cudaGetLastError();
 }
 

@@ -35,23 +35,28 @@ SLAB3D_4LVL = dict(
     theta0=-60.0, theta1=60.0, ell=0.1, M=256,
     N=[256, 64, 16, 4], seed=0, **COMMON)
 
-# The paper's own discretisation and model on its cube set-up (Sec. 3.2-3.3,
-# Sec. 4 and the cube hierarchy of Sec. 4.2): the unit cube, h = 0.2 .. 0.025
-# (5 .. 40 cells per axis), dt = 0.04 .. 0.005 ms over T = 1 ms, Crank-Nicolson
-# blocks, the FHN current with alpha = 1.4e-3, u_rest = 0, u_th = 28,
-# u_peak = 115 in units of u_peak (c = alpha u_peak^2, a = u_th / u_peak),
-# conductivity G0 = 3.325e-3 perturbed by the KL field, u(x, 0) = 0 and the
-# applied current u_peak exp(-|x - x0|^2 / sigma^2) (sigma = 0.5) on
-# [0, t1), t1 = 0.005 ms, in units of u_peak (amplitude 1); QoI u(x, T).
-# The stimulus centre x0 is the corner (the paper shows it only in a figure).
+# The paper's own discretisation and model on its cube set-up (Sec. 3.1.1,
+# Sec. 3.2-3.3, Sec. 4 and the cube hierarchy of Sec. 4.2): the unit cube,
+# h = 0.2 .. 0.025 (5 .. 40 cells per axis), dt = 0.04 .. 0.005 ms over
+# T = 1 ms, Crank-Nicolson blocks, the FHN current with alpha = 1.4e-3,
+# u_rest = 0, u_th = 28, u_peak = 115 in units of u_peak (c = alpha u_peak^2,
+# a = u_th / u_peak), the isotropic conductivity G = G0 (1 + s Z), G0 = 3.325e-3,
+# Z the affine KL field of the Gaussian kernel exp(-d^2 / sigma_KL) with
+# sigma_KL = 0.25 (ell = 0.5 in exp(-d^2/ell^2)), 66 pivoted-Cholesky modes on
+# the level-1 centroids, y ~ U(-1, 1), s = 0.3 capped by delta = 0.5;
+# u(x, 0) = 0 and the applied current u_peak exp(-|x - x0|^2 / sigma^2)
+# (sigma = 0.5) on [0, t1), t1 = 0.005 ms, in units of u_peak (amplitude 1);
+# QoI u(x, T).  The stimulus centre x0 is the corner (the paper shows it only
+# in a figure).
 FHN_ALPHA, FHN_UTH, FHN_UPEAK = 1.4e-3, 28.0, 115.0
 CUBE_CN_4LVL = dict(
-    name="mlmc3d_cube_cn_fhn_5-40_m25-200_M64",
+    name="mlmc3d_cube_cn_fhn_5-40_m25-200_affineKL66",
     dim=3, L=(1.0, 1.0, 1.0), n0=(5, 5, 5), m0=25, levels=4,
-    theta0=0.0, theta1=0.0, ell=0.25, M=64, N=[512, 128, 32, 8], seed=0,
+    theta0=0.0, theta1=0.0, ell=0.5, M=66, N=[512, 128, 32, 8], seed=0,
     T=1.0, c=FHN_ALPHA * FHN_UPEAK ** 2, a=FHN_UTH / FHN_UPEAK,
-    s_t=3.325e-3, s_l0=3.325e-3, stim_r=0.0, stim_c=(0.0, 0.0, 0.0), sigma2=0.04,
-    scheme=1, stim_kind=1, stim_amp=1.0, stim_sigma=0.5, stim_t1=0.005, qoi=1)
+    s_t=3.325e-3, s_l0=3.325e-3, stim_r=0.0, stim_c=(0.0, 0.0, 0.0), sigma2=1.0,
+    scheme=1, stim_kind=1, stim_amp=1.0, stim_sigma=0.5, stim_t1=0.005, qoi=1,
+    kl_kind=1, kl_tol=0.0, kl_s=0.3, kl_delta=0.5, kl_cand_level=1)
 
 WORKLOADS = {w["name"]: w for w in (MC2D_32, MLMC2D_3LVL, SLAB3D_4LVL, CUBE_CN_4LVL)}
 

@@ -13,6 +13,8 @@ def oracle_level(w, l, **kw):
     for key in ("scheme", "stim_kind", "stim_amp", "stim_sigma", "stim_t1", "qoi"):
         if key in w and key not in kw:
             kw[key] = w[key]
+    if w.get("kl_kind", 0) == 1 and "cond_kind" not in kw:
+        kw["cond_kind"] = 1
     return O.make_level(w["dim"], n, m, w["L"], w["T"], w["c"], w["a"], w["s_t"], w["s_l0"],
                         w["theta0"], w["theta1"], w["stim_r"], w["stim_c"], **kw)
 
@@ -47,13 +49,15 @@ def dense_K(lv, kst):
     dim = lv.dim
     N = [lv.n[d] + 1 for d in range(dim)] + [1] * (3 - dim)
     nodes = lv.nodes
-    no = 27 if dim == 3 else 9
+    no = 3 ** dim
     K = np.zeros((nodes, nodes))
     kst = kst.reshape(nodes, no)
     for A in range(nodes):
         i, j, k = A % N[0], (A // N[0]) % N[1], A // (N[0] * N[1])
         for o in range(no):
-            di, dj, dk = o % 3 - 1, (o // 3) % 3 - 1, (o // 9 - 1) if dim == 3 else 0
+            di = o % 3 - 1
+            dj = (o // 3) % 3 - 1 if dim >= 2 else 0
+            dk = (o // 9 - 1) if dim == 3 else 0
             ii, jj, kk = i + di, j + dj, k + dk
             if 0 <= ii < N[0] and 0 <= jj < N[1] and 0 <= kk < N[2]:
                 K[A, (kk * N[1] + jj) * N[0] + ii] += kst[A, o]
@@ -106,3 +110,21 @@ def fiber_D(dim, n, L, th0, th1, s_t, s_l0, Z):
         sl = s_l0 * math.exp(Z[ci])
         out.append(s_t * np.eye(dim) + (sl - s_t) * np.outer(f, f))
     return out
+
+
+def affine_kl(w):
+    """The oracle's KL of a workload with the paper's variant (kl_kind 1)."""
+    ns = [W.level_shape(w, l)[0] for l in range(w["levels"])]
+    return O.AffineKL(w["dim"], w["L"], ns[w["kl_cand_level"]], ns, w["sigma2"], w["ell"], w["M"],
+                      w["kl_tol"], w["kl_s"], w["kl_delta"])
+
+
+def oracle_field(w, level, seed, pair_level, sample_id, akl=None):
+    """The oracle's KL field of one sample on `level` (xi / psi drawn for the
+    pair `pair_level`), for either KL kind."""
+    if w.get("kl_kind", 0) == 1:
+        akl = akl or affine_kl(w)
+        return akl.field(level, O.psi_uniform(seed, pair_level, sample_id, w["M"]))[0]
+    n, _ = W.level_shape(w, level)
+    return O.kl_field(w["dim"], w["L"], n, w["sigma2"], w["ell"], w["M"],
+                      O.xi(seed, pair_level, sample_id, w["M"]))[0]

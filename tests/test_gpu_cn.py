@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import oracle_level, small_workload
+from helpers import oracle_field, oracle_level, small_workload
 from paper_1911_06066_gb300 import binding as B
 from paper_1911_06066_gb300 import workloads as W
 
@@ -57,8 +57,8 @@ def compare(w, level, ids, layout, precision=B.MLMC_PREC_FP64, u_tol=1e-8, q_tol
     lv = oracle_level(w, level)
     for r, i in enumerate(ids):
         assert B.info_dicts(info)[r]["status"] == 0
-        Zo = O.kl_field(w["dim"], w["L"], list(lv.n)[:w["dim"]], w["sigma2"], w["ell"], w["M"],
-                        O.xi(0, level, i, w["M"]))[0]
+        Zo = oracle_field(w, level, 0, level, i)
+        assert np.abs(Z[r].cpu().numpy() - Zo).max() <= 1e-12 * max(1.0, np.abs(Zo).max())
         so, qo, _ = O.solve_sample(lv, Zo)
         assert np.abs(slab[r].cpu().numpy() - so).max() <= u_tol
         assert np.abs(q[r].cpu().numpy() - qo).max() <= q_tol
