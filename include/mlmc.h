@@ -121,7 +121,9 @@ typedef struct {
   double kl_tol;         /* pivoted Cholesky stops at a remainder trace <= kl_tol x trace */
   double kl_s;           /* s of G = G0 (1 + s Z), capped by the ellipticity rule:        */
   double kl_delta;       /*   s_eff = min(kl_s, kl_delta / max_x sum_k |l_k(x)|)         */
-  int kl_cand_level;     /* level whose cell centroids are the pivot candidates           */
+  int kl_cand_n[3];      /* cells per axis of the grid whose cell centroids are the pivot
+                            candidates (zeros: level 0's grid); independent of the levels,
+                            so that contexts of different hierarchies share one field    */
 } mlmc_config;
 
 /* Random field of the conductivity.
@@ -132,7 +134,7 @@ typedef struct {
  *   Z = sum_k l_k(x) y_k, y_k ~ U(-1, 1) (from the same Philox words: 2u - 1),
  *   l_k the columns of the pivoted Cholesky factor (Harbrecht, Peters &
  *   Schneider 2012) of kl_sigma2 exp(-|x - x'|^2 / kl_ell^2) over the cell
- *   centroids of level kl_cand_level (at most kl_modes columns, fewer when the
+ *   centroids of the kl_cand_n grid (at most kl_modes columns, fewer when the
  *   remainder trace falls to kl_tol of the trace), extended to every level's
  *   centroids by the factor's own recursion (Nystrom), so that both members of
  *   a pair see the same continuous field; s_eff keeps G within

@@ -237,17 +237,19 @@ class AffineKL:
     Z(x, y) = sum_k l_k(x) y_k with l_k the pivoted-Cholesky columns of the
     Gaussian covariance, pivots chosen among the cell centroids of the
     candidate grid `cand_n`, extended to every level's centroids; G = G0 (1 +
-    s_eff Z) with s_eff = min(s, delta / max_x sum_k |l_k(x)|) over all levels'
-    centroids."""
+    s_eff Z) with s_eff = min(s, delta / max_x sum_k |l_k(x)|), the max over the
+    candidate centroids."""
 
     def __init__(self, dim, L, cand_n, level_ns, sigma2, ell, M, tol, s, delta):
         self.dim, self.L, self.M = dim, list(L), M
         X = cell_centroids(dim, L, cand_n)
-        self.m, self.piv, self.Lpiv, _ = pivoted_cholesky(X, sigma2, ell, M, tol)
+        self.m, self.piv, self.Lpiv, Lc = pivoted_cholesky(X, sigma2, ell, M, tol, want_L=True)
         self.Xp = X[self.piv]
         self.Phi = [pc_eval(cell_centroids(dim, L, n), self.Xp, sigma2, ell, M, self.m, self.Lpiv)
                     for n in level_ns]
-        bound = max(float(np.abs(P).sum(axis=1).max()) for P in self.Phi)
+        # the sup over x of sum_k |l_k(x)|, taken on the candidate grid (shared
+        # by every hierarchy that uses the same grid)
+        bound = float(np.abs(Lc).sum(axis=1).max())
         self.s_eff = min(s, delta / bound)
 
     def field(self, level, psi):

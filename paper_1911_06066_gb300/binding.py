@@ -36,7 +36,7 @@ class mlmc_config(C.Structure):
                 ("time_scheme", C.c_int), ("stim_kind", C.c_int), ("stim_amp", C.c_double),
                 ("stim_sigma", C.c_double), ("stim_t1", C.c_double), ("qoi", C.c_int),
                 ("kl_kind", C.c_int), ("kl_tol", C.c_double), ("kl_s", C.c_double),
-                ("kl_delta", C.c_double), ("kl_cand_level", C.c_int)]
+                ("kl_delta", C.c_double), ("kl_cand_n", C.c_int * 3)]
 
 
 MLMC_SOLVER_AUTO, MLMC_SOLVER_BLOCK, MLMC_SOLVER_CLUSTER = 0, 1, 2
@@ -258,12 +258,13 @@ def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, 
     c.stim_t1 = float(w.get("stim_t1", 0.0))
     c.qoi = int(w.get("qoi", MLMC_QOI_ACTIVATION))
     # the paper's KL variant (workload keys kl_kind / kl_tol / kl_s / kl_delta /
-    # kl_cand_level; sigma2 and ell then describe the Gaussian covariance)
+    # kl_cand_n; sigma2 and ell then describe the Gaussian covariance)
     c.kl_kind = int(w.get("kl_kind", MLMC_KL_SEPARABLE_EXP))
     c.kl_tol = float(w.get("kl_tol", 0.0))
     c.kl_s = float(w.get("kl_s", 0.3))
     c.kl_delta = float(w.get("kl_delta", 0.5))
-    c.kl_cand_level = int(w.get("kl_cand_level", 0))
+    for d, v in enumerate(w.get("kl_cand_n", (0, 0, 0))):
+        c.kl_cand_n[d] = int(v)
     return c
 
 

@@ -61,7 +61,7 @@ bool mlmc::level_mixed(const mlmc_config& c, const LevelDesc& lv) {
 static bool level_gmg(const mlmc_config& c, const LevelDesc& lv, MGDesc* mg) {
   mg->G = 0;
   mg->per_sample = 0;
-  if (c.precond != MLMC_PRECOND_GMG) return false;
+  if (c.precond != MLMC_PRECOND_GMG || lv.dim < 2) return false;
   double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
   if (lv.dt * rmax >= 1.0) return false;
   mg_hierarchy(lv, c.mg_nu > 0 ? c.mg_nu : 2, c.mg_coarse_sweeps > 0 ? c.mg_coarse_sweeps : 8, mg);
@@ -198,7 +198,7 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   *out = nullptr;
   if (!cfg) return fail(nullptr, MLMC_ERR_ARG, "cfg is NULL");
   const mlmc_config& c = *cfg;
-  if (c.dim != 2 && c.dim != 3) return fail(nullptr, MLMC_ERR_ARG, "dim must be 2 or 3");
+  if (c.dim < 1 || c.dim > 3) return fail(nullptr, MLMC_ERR_ARG, "dim must be 1, 2 or 3");
   if (c.n_levels < 1 || c.n_levels > MLMC_MAX_LEVELS)
     return fail(nullptr, MLMC_ERR_ARG, "n_levels out of range");
   for (int d = 0; d < c.dim; ++d)
@@ -223,10 +223,17 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   if (!model_config_ok(c)) return fail(nullptr, MLMC_ERR_ARG, "time scheme, stimulus or QoI out of range");
   if (c.kl_kind != MLMC_KL_SEPARABLE_EXP && c.kl_kind != MLMC_KL_AFFINE_GAUSSIAN)
     return fail(nullptr, MLMC_ERR_ARG, "unknown KL kind");
-  if (c.kl_kind == MLMC_KL_AFFINE_GAUSSIAN &&
-      (!(c.kl_tol >= 0.0) || !(c.kl_s >= 0.0) || !(c.kl_delta > 0.0 && c.kl_delta < 1.0) ||
-       c.kl_cand_level < 0 || c.kl_cand_level >= c.n_levels))
-    return fail(nullptr, MLMC_ERR_ARG, "affine KL parameters out of range");
+  if (c.kl_kind == MLMC_KL_AFFINE_GAUSSIAN) {
+    if (!(c.kl_tol >= 0.0) || !(c.kl_s >= 0.0) || !(c.kl_delta > 0.0 && c.kl_delta < 1.0))
+      return fail(nullptr, MLMC_ERR_ARG, "affine KL parameters out of range");
+    int64_t cand = 1;
+    for (int d = 0; d < c.dim; ++d) {
+      if (c.kl_cand_n[d] < 0 || c.kl_cand_n[d] > (1 << 20))
+        return fail(nullptr, MLMC_ERR_ARG, "affine KL candidate grid out of range");
+      cand *= c.kl_cand_n[d] ? c.kl_cand_n[d] : c.n0[d];
+    }
+    if (cand > (int64_t)1 << 22) return fail(nullptr, MLMC_ERR_ARG, "affine KL candidate grid too large");
+  }
 
   mlmc_ctx* ctx = new mlmc_ctx();
   ctx->cfg = c;
@@ -263,36 +270,29 @@ extern "C" mlmc_status mlmc_create(const mlmc_config* cfg, mlmc_ctx** out) {
   if ((e = cudaMalloc(&ctx->d_sqrt_lam, sizeof(double) * c.kl_modes)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
   if ((e = cudaMalloc(&ctx->d_idx, sizeof(int) * 3 * c.kl_modes)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
   if (affine) {
-    // the paper's KL: pivoted Cholesky on the candidate level's centroids,
+    // the paper's KL: pivoted Cholesky on the candidate grid's centroids,
     // the mode tables of every level, s_eff = min(s, delta / max sum |l_k|)
-    LevelDesc cand;
-    std::string why;
-    if (!derive_level(c, c.kl_cand_level, &cand, &why)) { mlmc_destroy(ctx); return fail(nullptr, MLMC_ERR_ARG, why); }
+    // with the max over the candidates
+    int cand_n[3] = {1, 1, 1};
+    for (int d = 0; d < c.dim; ++d) cand_n[d] = c.kl_cand_n[d] ? c.kl_cand_n[d] : c.n0[d];
     std::vector<double> xp, lpiv;
-    ctx->kl_rank = pivoted_cholesky_host(c.dim, c.L, cand.n, c.kl_sigma2, c.kl_ell, c.kl_modes,
-                                         c.kl_tol, xp, lpiv);
+    double bound = 0.0;
+    ctx->kl_rank = pivoted_cholesky_host(c.dim, c.L, cand_n, c.kl_sigma2, c.kl_ell, c.kl_modes,
+                                         c.kl_tol, xp, lpiv, &bound);
     if (ctx->kl_rank < 1) { mlmc_destroy(ctx); return fail(nullptr, MLMC_ERR_ARG, "KL factor has rank 0"); }
-    unsigned long long* d_bound = nullptr;
     if ((e = cudaMalloc(&ctx->d_xp, sizeof(double) * xp.size())) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&ctx->d_lpiv, sizeof(double) * lpiv.size())) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&d_bound, sizeof(unsigned long long))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
     if ((e = cudaMemcpy(ctx->d_xp, xp.data(), sizeof(double) * xp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
     if ((e = cudaMemcpy(ctx->d_lpiv, lpiv.data(), sizeof(double) * lpiv.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
-    if ((e = cudaMemset(d_bound, 0, sizeof(unsigned long long))) != cudaSuccess) return cleanup_fail(e, "cudaMemset");
     for (int l = 0; l < c.n_levels; ++l) {
       const size_t cnt = (size_t)ctx->lv[l].cells * c.kl_modes;
       if ((e = cudaMalloc(&ctx->d_tab64[l], sizeof(double) * cnt)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
       if ((e = cudaMalloc(&ctx->d_tab32[l], sizeof(float) * cnt)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc");
       if ((e = launch_pc_eval(ctx->lv[l], c.kl_modes, ctx->kl_rank, c.kl_sigma2, c.kl_ell, ctx->d_xp,
-                              ctx->d_lpiv, ctx->d_tab64[l], ctx->d_tab32[l], d_bound, nullptr)) != cudaSuccess)
+                              ctx->d_lpiv, ctx->d_tab64[l], ctx->d_tab32[l], nullptr, nullptr)) != cudaSuccess)
         return cleanup_fail(e, "pc_eval");
     }
-    unsigned long long bits = 0;
-    e = cudaMemcpy(&bits, d_bound, sizeof bits, cudaMemcpyDeviceToHost);
-    cudaFree(d_bound);
-    if (e != cudaSuccess) return cleanup_fail(e, "cudaMemcpy");
-    double bound;
-    memcpy(&bound, &bits, sizeof bound);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup_fail(e, "pc_eval");
     ctx->kl_s_eff = bound > 0.0 ? fmin(c.kl_s, c.kl_delta / bound) : c.kl_s;
     for (int q = 0; q < c.kl_modes; ++q) sl[q] = ctx->kl_s_eff;
   }

@@ -24,6 +24,7 @@ __device__ inline double sgn(int b) { return b ? 1.0 : -1.0; }
 
 __device__ double element_entry(int dim, const double D[3][3], const double h[3], const int a[3],
                                 const int b[3]) {
+  if (dim == 1) return D[0][0] * sgn(a[0]) * sgn(b[0]) / h[0];
   if (dim == 2) {
     return D[0][0] * sgn(a[0]) * sgn(b[0]) * (h[1] / h[0]) * m1(a[1], b[1]) +
            D[1][1] * sgn(a[1]) * sgn(b[1]) * (h[0] / h[1]) * m1(a[0], b[0]) +
@@ -45,7 +46,7 @@ __device__ double element_entry(int dim, const double D[3][3], const double h[3]
 template <int DIM>
 __global__ void assemble_kernel(LevelDesc lv, Physics ph, const double* __restrict__ Z, int n,
                                 double* __restrict__ coef64, float* __restrict__ coef32) {
-  constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)n * lv.nodes) return;
   int s = (int)(g / lv.nodes);
@@ -57,7 +58,7 @@ __global__ void assemble_kernel(LevelDesc lv, Physics ph, const double* __restri
   for (int o = 0; o < NO; ++o) K[o] = 0.0;
   const double* Zs = Z + (int64_t)s * lv.cells;
   for (int cz = (DIM == 3 ? -1 : 0); cz <= 0; ++cz)
-    for (int cy = -1; cy <= 0; ++cy)
+    for (int cy = (DIM >= 2 ? -1 : 0); cy <= 0; ++cy)
       for (int cx = -1; cx <= 0; ++cx) {
         int cell[3] = {ijk[0] + cx, ijk[1] + cy, ijk[2] + cz};
         bool ok = true;
@@ -79,10 +80,11 @@ __global__ void assemble_kernel(LevelDesc lv, Physics ph, const double* __restri
         }
         int a[3] = {-cx, -cy, -cz};
         for (int bz = 0; bz < (DIM == 3 ? 2 : 1); ++bz)
-          for (int by = 0; by < 2; ++by)
+          for (int by = 0; by < (DIM >= 2 ? 2 : 1); ++by)
             for (int bx = 0; bx < 2; ++bx) {
               int b[3] = {bx, by, bz};
-              int o = (bx - a[0] + 1) + 3 * (by - a[1] + 1) + (DIM == 3 ? 9 * (bz - a[2] + 1) : 0);
+              int o = (bx - a[0] + 1) + (DIM >= 2 ? 3 * (by - a[1] + 1) : 0) +
+                      (DIM == 3 ? 9 * (bz - a[2] + 1) : 0);
               K[o] += element_entry(DIM, D, lv.h, a, b);
             }
       }
@@ -105,14 +107,17 @@ cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double
   unsigned grid = (unsigned)((total + bs - 1) / bs);
   if (lv.dim == 3)
     assemble_kernel<3><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32);
-  else
+  else if (lv.dim == 2)
     assemble_kernel<2><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32);
+  else
+    assemble_kernel<1><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32);
   return cudaGetLastError();
 }
 
 cudaError_t preload_assemble() {
   cudaFuncAttributes a;
   cudaError_t e = cudaFuncGetAttributes(&a, assemble_kernel<2>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, assemble_kernel<1>);
   return e == cudaSuccess ? cudaFuncGetAttributes(&a, assemble_kernel<3>) : e;
 }
 

@@ -62,7 +62,7 @@ __device__ __forceinline__ void coords(const MGLevel& L, int f, int& i, int& j, 
 template <int DIM, typename TA, typename TK, typename TX>
 __device__ __forceinline__ TA apply_K(const TK* K, const MGLevel& L, int f, int i, int j, int k,
                                       const TX* x) {
-  constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
   const int64_t n = L.nodes;
   const int N0 = L.N[0], N01 = L.N[0] * L.N[1];
   TA y = 0;
@@ -71,13 +71,13 @@ __device__ __forceinline__ TA apply_K(const TK* K, const MGLevel& L, int f, int 
   if (in) {
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
-      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+      const int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
       y += (TA)K[o * n + f] * (TA)x[f + dx + dy * N0 + dz * N01];
     }
   } else {
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
-      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+      const int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
       const int ii = i + dx, jj = j + dy, kk = k + dz;
       if (ii < 0 || ii >= L.N[0] || jj < 0 || jj >= L.N[1] || kk < 0 || kk >= L.N[2]) continue;
       y += (TA)K[o * n + f] * (TA)x[f + dx + dy * N0 + dz * N01];
@@ -115,7 +115,7 @@ __device__ __forceinline__ int coarse_support(int f, int halved, int* idx, doubl
 template <int DIM, typename TK, typename KR>
 __device__ void galerkin_node(const TK* Kf, const MGLevel& Lf, const MGLevel& Lc, int c, int ci,
                               int cj, int ck, KR* Kc, KR* ks) {
-  constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
   double acc[NO];
 #pragma unroll
   for (int o = 0; o < NO; ++o) acc[o] = 0.0;
@@ -133,7 +133,7 @@ __device__ void galerkin_node(const TK* Kf, const MGLevel& Lf, const MGLevel& Lc
         const double wf = wx[e] * wy[b] * wz[a];
         const int f = fx[e] + Lf.N[0] * (fy[b] + Lf.N[1] * fz[a]);
         for (int o = 0; o < NO; ++o) {
-          const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+          const int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
           const int gi = fx[e] + dx, gj = fy[b] + dy, gk = fz[a] + dz;
           if (gi < 0 || gi >= Lf.N[0] || gj < 0 || gj >= Lf.N[1] || gk < 0 || gk >= Lf.N[2]) continue;
           const double kv = (double)Kf[o * nf + f];
@@ -208,7 +208,7 @@ __device__ __forceinline__ KR prolong_node(const KR* x, const MGLevel& Lf, const
 template <int NT, int DIM, typename KR>
 __device__ void build(const MGDesc& mg, KR* blk, const double* K0, cgx::cluster_group& cl, int C,
                       int rank) {
-  constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
   {
     const MGLevel& L = mg.l[0];
     const Range r = range(L.nodes, C, rank);

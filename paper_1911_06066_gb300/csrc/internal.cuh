@@ -137,15 +137,15 @@ struct MGDesc {
 void mg_hierarchy(const LevelDesc& lv, int nu, int coarse_sweeps, MGDesc* mg);
 
 // Number of stencil couplings per node (3^dim) and the centre index.
-__host__ __device__ inline int n_offsets(int dim) { return dim == 3 ? 27 : 9; }
-__host__ __device__ inline int centre_offset(int dim) { return dim == 3 ? 13 : 4; }
+__host__ __device__ inline int n_offsets(int dim) { return dim == 3 ? 27 : (dim == 2 ? 9 : 3); }
+__host__ __device__ inline int centre_offset(int dim) { return dim == 3 ? 13 : (dim == 2 ? 4 : 1); }
 
 // Lumped Q1 mass of node (i,j,k): cell volume times 1/2 per axis on which the
 // node lies on the boundary (the row sum of the consistent mass).
 __device__ inline double lumped_mass(const LevelDesc& lv, int i, int j, int k) {
   double m = lv.vol;
   if (i == 0 || i == lv.n[0]) m *= 0.5;
-  if (j == 0 || j == lv.n[1]) m *= 0.5;
+  if (lv.dim >= 2 && (j == 0 || j == lv.n[1])) m *= 0.5;
   if (lv.dim == 3 && (k == 0 || k == lv.n[2])) m *= 0.5;
   return m;
 }
@@ -180,13 +180,15 @@ cudaError_t launch_xi(uint64_t seed, const uint64_t* seeds, int level, const uin
 // Gaussian covariance sigma2 exp(-|x - x'|^2 / ell^2) on the cell centroids of
 // an n[3] grid (at most M columns; stop at a remainder trace <= tol of the
 // full trace): the pivot coordinates xp [m][3] and the pivot rows of the
-// factor lpiv [M][M]; returns the rank m.
+// factor lpiv [M][M]; *bound = max over the candidates of sum_k |L_ck| (the
+// ellipticity rule's sup); returns the rank m.
 int pivoted_cholesky_host(int dim, const double* L, const int* n, double sigma2, double ell, int M,
-                          double tol, std::vector<double>& xp, std::vector<double>& lpiv);
+                          double tol, std::vector<double>& xp, std::vector<double>& lpiv,
+                          double* bound);
 // Device: the factor's columns at the cell centroids of lv (Nystrom
-// extension), phi64 [cells][M] and phi32 (same in FP32, may be NULL); and the
-// largest sum_k |phi_k| over the cells into *bound (device, atomic max on the
-// bits of a non-negative double; zero it first).
+// extension), phi64 [cells][M] and phi32 (same in FP32, may be NULL); bound
+// (device, may be NULL): the largest sum_k |phi_k| over the cells (atomic max
+// on the bits of a non-negative double; zero it first).
 cudaError_t launch_pc_eval(const LevelDesc& lv, int M, int m, double sigma2, double ell,
                            const double* xp, const double* lpiv, double* phi64, float* phi32,
                            unsigned long long* bound, cudaStream_t st);

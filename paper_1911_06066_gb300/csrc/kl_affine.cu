@@ -27,7 +27,8 @@
 namespace mlmc {
 
 int pivoted_cholesky_host(int dim, const double* L, const int* n, double sigma2, double ell, int M,
-                          double tol, std::vector<double>& xp, std::vector<double>& lpiv) {
+                          double tol, std::vector<double>& xp, std::vector<double>& lpiv,
+                          double* bound) {
   const int64_t cells = (int64_t)n[0] * (dim >= 2 ? n[1] : 1) * (dim >= 3 ? n[2] : 1);
   std::vector<double> X((size_t)cells * 3, 0.0);
   for (int64_t c = 0; c < cells; ++c) {
@@ -67,6 +68,16 @@ int pivoted_cholesky_host(int dim, const double* L, const int* n, double sigma2,
     for (int64_t c = 0; c < cells; ++c) rem[c] -= fac[(size_t)c * M + m] * fac[(size_t)c * M + m];
     rem[p] = 0.0;
   }
+  // max over the candidates of sum_k |L_ck|: the ellipticity bound's sup over
+  // x, taken on the candidate grid so that every hierarchy sharing the grid
+  // gets the same s_eff
+  double b = 0.0;
+  for (int64_t c = 0; c < cells; ++c) {
+    double sa = 0.0;
+    for (int j = 0; j < m; ++j) sa += fabs(fac[(size_t)c * M + j]);
+    b = sa > b ? sa : b;
+  }
+  *bound = b;
   xp.assign((size_t)m * 3, 0.0);
   lpiv.assign((size_t)M * M, 0.0);
   for (int a = 0; a < m; ++a) {

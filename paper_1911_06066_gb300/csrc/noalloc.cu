@@ -78,7 +78,7 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int level, con
                                           void* stream) {
   if (!cfg) return reject(MLMC_ERR_ARG, "cfg is NULL");
   const mlmc_config& c = *cfg;
-  if (c.dim != 2 && c.dim != 3) return reject(MLMC_ERR_ARG, "dim must be 2 or 3");
+  if (c.dim < 1 || c.dim > 3) return reject(MLMC_ERR_ARG, "dim must be 1, 2 or 3");
   if (level < 0 || level >= c.n_levels || c.n_levels > MLMC_MAX_LEVELS)
     return reject(MLMC_ERR_ARG, "level out of range");
   if (!(c.kl_sigma2 >= 0.0) || c.precond < MLMC_PRECOND_JACOBI || c.precond > MLMC_PRECOND_GMG)

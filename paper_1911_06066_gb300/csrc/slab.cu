@@ -21,7 +21,7 @@ template <int DIM>
 __global__ void slab_residual_kernel(LevelDesc lv, Physics ph, const double* __restrict__ coef64,
                                      const double* __restrict__ slab, double* __restrict__ F,
                                      unsigned long long* __restrict__ res_max) {
-  constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
   __shared__ double wmax[32];
   const int64_t N = lv.nodes;
   const int s = blockIdx.y;                       // one sample per grid row
@@ -37,7 +37,7 @@ __global__ void slab_residual_kernel(LevelDesc lv, Physics ph, const double* __r
     double ku = 0.0;
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
-      int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+      int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
       int64_t B = A + dx + (int64_t)lv.N[0] * (dy + (int64_t)lv.N[1] * dz);
       B = B < 0 ? 0 : (B >= N ? N - 1 : B);
       ku += c[(int64_t)o * N + A] * u[B];
@@ -47,7 +47,7 @@ __global__ void slab_residual_kernel(LevelDesc lv, Physics ph, const double* __r
     if (c_up != 0.0) {
 #pragma unroll
       for (int o = 0; o < NO; ++o) {
-        int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+        int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
         int64_t B = A + dx + (int64_t)lv.N[0] * (dy + (int64_t)lv.N[1] * dz);
         B = B < 0 ? 0 : (B >= N ? N - 1 : B);
         ku += c_up * c[(int64_t)o * N + A] * up[B];
@@ -94,8 +94,10 @@ cudaError_t launch_slab_residual(const LevelDesc& lv, const Physics& ph, const d
   dim3 grid((unsigned)((per_sample + bs - 1) / bs), (unsigned)n);
   if (lv.dim == 3)
     slab_residual_kernel<3><<<grid, bs, 0, st>>>(lv, ph, coef64, slab, F, (unsigned long long*)res_max);
-  else
+  else if (lv.dim == 2)
     slab_residual_kernel<2><<<grid, bs, 0, st>>>(lv, ph, coef64, slab, F, (unsigned long long*)res_max);
+  else
+    slab_residual_kernel<1><<<grid, bs, 0, st>>>(lv, ph, coef64, slab, F, (unsigned long long*)res_max);
   return cudaGetLastError();
 }
 

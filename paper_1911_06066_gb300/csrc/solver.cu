@@ -81,7 +81,7 @@ __device__ double block_max(double v, double* sh) {
 
 template <int DIM>
 __device__ __forceinline__ int64_t nb_offset(const LevelDesc& lv, int o) {
-  int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+  int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
   return dx + (int64_t)lv.N[0] * (dy + (int64_t)lv.N[1] * dz);
 }
 
@@ -90,7 +90,7 @@ __device__ __forceinline__ int64_t nb_offset(const LevelDesc& lv, int o) {
 template <int DIM, typename TC, typename TV, typename TA>
 __device__ __forceinline__ TA stencil(const LevelDesc& lv, const TC* __restrict__ c,
                                       const TV* __restrict__ v, int64_t A) {
-  constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
   TA y = 0;
 #pragma unroll
   for (int o = 0; o < NO; ++o) {
@@ -107,7 +107,7 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
              const KR* __restrict__ coefK, double* slab, double* ubuf, double* Fb, double* Kub,
              double* Kdb, KR* krb, double* t_act, mlmc_sample_info* info,
              unsigned long long* counters) {
-  constexpr int NO = DIM == 3 ? 27 : 9;
+  constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
   __shared__ double sh[SOLVE_THREADS / 32];
   const int s = blockIdx.x;
   const int64_t N = lv.nodes;
@@ -351,31 +351,31 @@ cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverPar
                          void* kr, double* t_act, mlmc_sample_info* info,
                          unsigned long long* counters, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+#define SOLVE_LAUNCH(KR, D, CK)                                                                  \
+  solve_kernel<KR, D><<<n, SOLVE_THREADS, 0, st>>>(lv, ph, sp, coef64, CK, slab, ubuf, F, Ku, Kd,  \
+                                                  (KR*)kr, t_act, info, counters)
   if (mixed) {
-    if (lv.dim == 3)
-      solve_kernel<float, 3><<<n, SOLVE_THREADS, 0, st>>>(lv, ph, sp, coef64, coef32, slab, ubuf, F,
-                                                          Ku, Kd, (float*)kr, t_act, info, counters);
-    else
-      solve_kernel<float, 2><<<n, SOLVE_THREADS, 0, st>>>(lv, ph, sp, coef64, coef32, slab, ubuf, F,
-                                                          Ku, Kd, (float*)kr, t_act, info, counters);
+    if (lv.dim == 3) SOLVE_LAUNCH(float, 3, coef32);
+    else if (lv.dim == 2) SOLVE_LAUNCH(float, 2, coef32);
+    else SOLVE_LAUNCH(float, 1, coef32);
   } else {
-    if (lv.dim == 3)
-      solve_kernel<double, 3><<<n, SOLVE_THREADS, 0, st>>>(lv, ph, sp, coef64, coef64, slab, ubuf, F,
-                                                           Ku, Kd, (double*)kr, t_act, info, counters);
-    else
-      solve_kernel<double, 2><<<n, SOLVE_THREADS, 0, st>>>(lv, ph, sp, coef64, coef64, slab, ubuf, F,
-                                                           Ku, Kd, (double*)kr, t_act, info, counters);
+    if (lv.dim == 3) SOLVE_LAUNCH(double, 3, coef64);
+    else if (lv.dim == 2) SOLVE_LAUNCH(double, 2, coef64);
+    else SOLVE_LAUNCH(double, 1, coef64);
   }
+#undef SOLVE_LAUNCH
   return cudaGetLastError();
 }
 
 cudaError_t preload_solve(const LevelDesc& lv, bool mixed) {
   cudaFuncAttributes a;
   if (mixed)
-    return lv.dim == 3 ? cudaFuncGetAttributes(&a, solve_kernel<float, 3>)
-                       : cudaFuncGetAttributes(&a, solve_kernel<float, 2>);
-  return lv.dim == 3 ? cudaFuncGetAttributes(&a, solve_kernel<double, 3>)
-                     : cudaFuncGetAttributes(&a, solve_kernel<double, 2>);
+    return lv.dim == 3   ? cudaFuncGetAttributes(&a, solve_kernel<float, 3>)
+           : lv.dim == 2 ? cudaFuncGetAttributes(&a, solve_kernel<float, 2>)
+                         : cudaFuncGetAttributes(&a, solve_kernel<float, 1>);
+  return lv.dim == 3   ? cudaFuncGetAttributes(&a, solve_kernel<double, 3>)
+         : lv.dim == 2 ? cudaFuncGetAttributes(&a, solve_kernel<double, 2>)
+                       : cudaFuncGetAttributes(&a, solve_kernel<double, 1>);
 }
 
 }  // namespace mlmc

@@ -23,7 +23,7 @@ size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt)
 // picks clusters of 16 CTAs, or fewer for grids of at most 8192 nodes.
 bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm) {
   const int rowlen = lv.dim == 3 ? lv.N[0] * lv.N[1] : lv.N[0];
-  const int nrows = lv.dim == 3 ? lv.N[2] : lv.N[1];
+  const int nrows = lv.dim == 3 ? lv.N[2] : lv.N[1];   // 1 in one dimension: one row
   const size_t limit = 224 * 1024;
   if (gm) {
     int C = want_C;
@@ -84,13 +84,21 @@ static cudaError_t max_clusters_one(const ClusterPlan& pl, int* count) {
 }
 
 cudaError_t preload_solve_cluster(const LevelDesc& lv, bool mixed, const ClusterPlan& pl) {
-  if (mixed) return lv.dim == 3 ? preload_one<float, 3>(pl) : preload_one<float, 2>(pl);
-  return lv.dim == 3 ? preload_one<double, 3>(pl) : preload_one<double, 2>(pl);
+  if (mixed)
+    return lv.dim == 3 ? preload_one<float, 3>(pl)
+                       : (lv.dim == 2 ? preload_one<float, 2>(pl) : preload_one<float, 1>(pl));
+  return lv.dim == 3 ? preload_one<double, 3>(pl)
+                     : (lv.dim == 2 ? preload_one<double, 2>(pl) : preload_one<double, 1>(pl));
 }
 
 cudaError_t cluster_max_active(const LevelDesc& lv, bool mixed, const ClusterPlan& pl, int* count) {
-  if (mixed) return lv.dim == 3 ? max_clusters_one<float, 3>(pl, count) : max_clusters_one<float, 2>(pl, count);
-  return lv.dim == 3 ? max_clusters_one<double, 3>(pl, count) : max_clusters_one<double, 2>(pl, count);
+  if (mixed)
+    return lv.dim == 3   ? max_clusters_one<float, 3>(pl, count)
+           : lv.dim == 2 ? max_clusters_one<float, 2>(pl, count)
+                         : max_clusters_one<float, 1>(pl, count);
+  return lv.dim == 3   ? max_clusters_one<double, 3>(pl, count)
+         : lv.dim == 2 ? max_clusters_one<double, 2>(pl, count)
+                       : max_clusters_one<double, 1>(pl, count);
 }
 
 cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
@@ -108,11 +116,15 @@ cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const S
   if (mixed) {
     if (lv.dim == 3)
       return launch_nt<float, 3>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, mg, st);
-    return launch_nt<float, 2>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, mg, st);
+    if (lv.dim == 2)
+      return launch_nt<float, 2>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, mg, st);
+    return launch_nt<float, 1>(lv, ph, sp, pl, n, coef64, coef32, slab, t_act, info, counters, g, mg, st);
   }
   if (lv.dim == 3)
     return launch_nt<double, 3>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, mg, st);
-  return launch_nt<double, 2>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, mg, st);
+  if (lv.dim == 2)
+    return launch_nt<double, 2>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, mg, st);
+  return launch_nt<double, 1>(lv, ph, sp, pl, n, coef64, coef64, slab, t_act, info, counters, g, mg, st);
 }
 
 // Multigrid hierarchy of grid lv (see MGDesc): level 0 is lv itself; every

@@ -89,8 +89,8 @@ __device__ __forceinline__ TA stencil_band(const Band& b, const View<TV>& v, int
                                            CF c) {
   TA y = 0;
 #pragma unroll
-  for (int o = 0; o < (DIM == 3 ? 27 : 9); ++o) {
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+  for (int o = 0; o < (DIM == 3 ? 27 : (DIM == 2 ? 9 : 3)); ++o) {
+    const int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
     const int ii = i + dx, jj = j + dy, kk = k + dz;
     if (ii < 0 || ii >= b.N0 || jj < 0 || jj >= b.N1 || kk < 0 || kk >= b.N2) continue;
     const int row = DIM == 3 ? kk : jj;
@@ -111,8 +111,8 @@ template <int DIM, typename TA, typename TV, typename CF>
 __device__ __forceinline__ TA stencil_fast(const TV* v, int a, int N0, int N01, CF c) {
   TA y = 0;
 #pragma unroll
-  for (int o = 0; o < (DIM == 3 ? 27 : 9); ++o) {
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
+  for (int o = 0; o < (DIM == 3 ? 27 : (DIM == 2 ? 9 : 3)); ++o) {
+    const int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
     y += (TA)c(o) * (TA)v[a + dx + dy * N0 + dz * N01];
   }
   return y;
@@ -197,8 +197,8 @@ __device__ __forceinline__ unsigned gm_code(const Band& b, int A) {
   const int i = A - jk * b.N0;
   const int k = jk / b.N1;
   const int j = jk - k * b.N1;
-  const bool in = i > 0 && i < b.N0 - 1 && j > 0 && j < b.N1 - 1 &&
-                  (DIM == 2 || (k > 0 && k < b.N2 - 1));
+  const bool in = i > 0 && i < b.N0 - 1 && (DIM < 2 || (j > 0 && j < b.N1 - 1)) &&
+                  (DIM <= 2 || (k > 0 && k < b.N2 - 1));
   return (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22) | (in ? 0x80000000u : 0u);
 }
 
@@ -247,8 +247,8 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
                      double* g_u, double* g_F, KR* g_kr, unsigned* g_code, const MGDesc mg,
                      KR* g_mg) {
   static_assert(!MG || GM, "the multigrid preconditioner needs the global-memory layout");
-  constexpr int NO = DIM == 3 ? 27 : 9;
-  constexpr int CTR = DIM == 3 ? 13 : 4;
+  constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
+  constexpr int CTR = DIM == 3 ? 13 : (DIM == 2 ? 4 : 1);
   cg::cluster_group cl = cg::this_cluster();
   Band b;
   b.C = (int)cl.num_blocks();
@@ -320,7 +320,8 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       if (DIM == 3) { k = row; j = inrow / b.N0; i = inrow - j * b.N0; }
       else { k = 0; j = row; i = inrow; }
     }
-    bool in = i > 0 && i < b.N0 - 1 && j > 0 && j < b.N1 - 1 && (DIM == 2 || (k > 0 && k < b.N2 - 1));
+    bool in = i > 0 && i < b.N0 - 1 && (DIM < 2 || (j > 0 && j < b.N1 - 1)) &&
+              (DIM <= 2 || (k > 0 && k < b.N2 - 1));
     bool fast = in && (GM || (row > b.row0 && row < b.row1 - 1));
     code[a] = (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22) | (fast ? 0x80000000u : 0u);
   }

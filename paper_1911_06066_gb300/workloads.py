@@ -43,7 +43,7 @@ SLAB3D_4LVL = dict(
 # a = u_th / u_peak), the isotropic conductivity G = G0 (1 + s Z), G0 = 3.325e-3,
 # Z the affine KL field of the Gaussian kernel exp(-d^2 / sigma_KL) with
 # sigma_KL = 0.25 (ell = 0.5 in exp(-d^2/ell^2)), 66 pivoted-Cholesky modes on
-# the level-1 centroids, y ~ U(-1, 1), s = 0.3 capped by delta = 0.5;
+# the level-1 centroids (10^3), y ~ U(-1, 1), s = 0.3 capped by delta = 0.5;
 # u(x, 0) = 0 and the applied current u_peak exp(-|x - x0|^2 / sigma^2)
 # (sigma = 0.5) on [0, t1), t1 = 0.005 ms, in units of u_peak (amplitude 1);
 # QoI u(x, T).  The stimulus centre x0 is the corner (the paper shows it only
@@ -56,7 +56,7 @@ CUBE_CN_4LVL = dict(
     T=1.0, c=FHN_ALPHA * FHN_UPEAK ** 2, a=FHN_UTH / FHN_UPEAK,
     s_t=3.325e-3, s_l0=3.325e-3, stim_r=0.0, stim_c=(0.0, 0.0, 0.0), sigma2=1.0,
     scheme=1, stim_kind=1, stim_amp=1.0, stim_sigma=0.5, stim_t1=0.005, qoi=1,
-    kl_kind=1, kl_tol=0.0, kl_s=0.3, kl_delta=0.5, kl_cand_level=1)
+    kl_kind=1, kl_tol=0.0, kl_s=0.3, kl_delta=0.5, kl_cand_n=(10, 10, 10))
 
 WORKLOADS = {w["name"]: w for w in (MC2D_32, MLMC2D_3LVL, SLAB3D_4LVL, CUBE_CN_4LVL)}
 

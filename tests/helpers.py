@@ -115,7 +115,8 @@ def fiber_D(dim, n, L, th0, th1, s_t, s_l0, Z):
 def affine_kl(w):
     """The oracle's KL of a workload with the paper's variant (kl_kind 1)."""
     ns = [W.level_shape(w, l)[0] for l in range(w["levels"])]
-    return O.AffineKL(w["dim"], w["L"], ns[w["kl_cand_level"]], ns, w["sigma2"], w["ell"], w["M"],
+    cand = tuple(c if c else n for c, n in zip(w["kl_cand_n"][:w["dim"]], w["n0"]))
+    return O.AffineKL(w["dim"], w["L"], cand, ns, w["sigma2"], w["ell"], w["M"],
                       w["kl_tol"], w["kl_s"], w["kl_delta"])
 
 

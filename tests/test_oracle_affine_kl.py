@@ -98,14 +98,17 @@ def test_extension_reproduces_the_factor_and_the_kernel():
 
 def test_ellipticity_cap_and_field_covariance():
     akl = O.AffineKL(2, [1.0, 1.0], (6, 6), [(6, 6), (12, 12)], 1.0, 0.5, 20, 0.0, 0.3, 0.5)
-    bound = max(np.abs(P).sum(1).max() for P in akl.Phi)
+    bound = np.abs(akl.Phi[0]).sum(1).max()       # level 0 is the candidate grid
     assert akl.s_eff == pytest.approx(min(0.3, 0.5 / bound))
     # the extreme inputs psi_k = sign(l_k(x)) reach the cap exactly at the
-    # maximising point and nowhere exceed it
-    for P in akl.Phi:
-        i = int(np.argmax(np.abs(P).sum(1)))
-        z = akl.s_eff * np.sign(P[i]) @ P.T
-        assert z.max() <= 0.5 + 1e-12
+    # maximising candidate and nowhere there exceed it; on a finer grid the
+    # field stays within a few per cent of the cap (the sup is taken on the
+    # candidates)
+    P = akl.Phi[0]
+    i = int(np.argmax(np.abs(P).sum(1)))
+    z = akl.s_eff * np.sign(P[i]) @ P.T
+    assert abs(z.max() - 0.5) < 1e-12
+    assert akl.s_eff * np.abs(akl.Phi[1]).sum(1).max() <= 0.5 * 1.05
     # covariance of Z: s_eff^2 / 3 Phi Phi^T (psi uniform, variance 1/3)
     rng_ids = range(6000)
     Zs = np.stack([akl.field(1, O.psi_uniform(3, 1, i, 20))[0] for i in rng_ids])
