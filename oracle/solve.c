@@ -27,16 +27,18 @@
  * convex implicit-Euler pseudo-steps); or_step_solve reaches the same point
  * faster by a gradient-flow continuation, and the tests pin the two together:
  *   - linearly implicit pseudo-steps (M/t + H(u)) d = -F(u), u += d, by
- *     Jacobi-preconditioned CG; t starts at 1/(2 max r') and doubles after
- *     every accepted step; a step whose CG meets non-positive curvature (M/t +
- *     H not positive definite) is retried with t/4.  A step with M/t + H
+ *     Jacobi-preconditioned CG; t starts at 1/(2 max r'); a step whose CG
+ *     meets non-positive curvature (M/t + H not positive definite) is retried
+ *     with t/4.  A step with M/t + H
  *     positive definite never reverses the sign of the flow's unstable
  *     component near a saddle (the linearised step multiplies it by
  *     1/(1 - t lambda_u) > 0), so it does not jump between basins, and t can
  *     grow as far as the local curvature allows -- near a nearly degenerate
  *     saddle, where the flow crawls, that is what makes the continuation fast;
- *   - a step that would move some node by more than FLOW_MOVE is retried with
- *     a shorter t (counted as a halving);
+ *   - a step that would move some node by more than FLOW_MOVE is taken
+ *     shortened to that move and the next t is scaled down accordingly
+ *     (counted as a halving); otherwise t grows towards the move limit, at
+ *     most doubling;
  *   - once an accepted step moves no node by more than FLOW_NEWTON the flow has
  *     arrived near its minimum, and Newton steps (t = infinity) finish it as
  *     long as their CG meets no non-positive curvature and they move no node
@@ -226,15 +228,20 @@ int or_step_solve(const or_level* lv, const double* mass, const double* Kst,
         continue;
       }
       if (dmax > FLOW_MOVE && t > FLOW_TMIN) {
-        /* the step would move a node by more than FLOW_MOVE: retry shorter */
-        tau = t * 0.5 * FLOW_MOVE / dmax;
+        /* the step would move a node by more than FLOW_MOVE: take it shortened
+           to that move (a positive multiple of the step keeps its sign along
+           every eigenvector of M/t + H) and continue with a shorter pseudo-step */
+        const double sc = FLOW_MOVE / dmax;
+        for (int i = 0; i < n; ++i) u[i] += sc * d[i];
+        tau = t * 0.9 * sc;
         ++halvings;
         continue;
       }
       for (int i = 0; i < n; ++i) u[i] += d[i];
       if (dmax <= lv->newton_tol) { conv = 1; break; }
       if (dmax <= sw) newton_phase = 1;
-      tau = fmin(2.0 * t, FLOW_TMAX);
+      /* grow towards the move limit, at most doubling */
+      tau = fmin(t * fmin(2.0, 0.9 * FLOW_MOVE / dmax), FLOW_TMAX);
       continue;
     }
     int cg = or_newton_cg(n, mass, Kst, lv, u, F, d, &tr);

@@ -71,15 +71,17 @@ struct SolverParams {
 // c((1+a)^2/3 - a)).  Such a step has several roots; the root is the end
 // point of the gradient flow M v' = -F(v) of the step energy from u_{k-1},
 // the local minimum in whose basin u_{k-1} lies.  It is reached by linearly
-// implicit pseudo-steps (M/t + H(u)) d = -F(u): t starts at tau0 and doubles
-// after each accepted step; a step whose CG meets non-positive curvature (M/t
-// + H not positive definite) is retried with t/4 -- with M/t + H positive
-// definite a step never reverses the flow's unstable component near a saddle
-// -- and a step moving a node by more than FLOW_MOVE is retried shorter; once
-// an accepted step moves no node by more than the switch threshold
-// (FLOW_NEWTON at first) Newton steps finish the solve while their CG meets
-// only positive curvature and they move no node by more than 10x the
-// threshold (else the flow resumes with a 10x smaller threshold).
+// implicit pseudo-steps (M/t + H(u)) d = -F(u): t starts at tau0; a step whose
+// CG meets non-positive curvature (M/t + H not positive definite) is retried
+// with t/4 -- with M/t + H positive definite a step never reverses the flow's
+// unstable component near a saddle; a step moving a node by more than
+// FLOW_MOVE is taken shortened to that move (a positive multiple of the same
+// direction) and the next t shrinks accordingly, otherwise t grows towards the
+// move limit, at most doubling; once an accepted step moves no node by more
+// than the switch threshold (FLOW_NEWTON at first) Newton steps finish the
+// solve while their CG meets only positive curvature and they move no node by
+// more than 10x the threshold (else the flow resumes with a 10x smaller
+// threshold).
 constexpr double FLOW_MOVE = 0.3;
 constexpr double FLOW_TMIN = 1e-9;
 constexpr double FLOW_TMAX = 1e20;

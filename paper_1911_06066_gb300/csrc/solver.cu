@@ -14,11 +14,12 @@
 // M v' = -F_k(v) from u_{k-1}: the minimum in whose basin u_{k-1} lies.
 //   * Levels with several roots (sp.flow): gradient-flow continuation by
 //     linearly implicit pseudo-steps (M/t + H(u)) d = -F(u), u += d, with the
-//     pseudo-step t growing x2 per accepted step from 1/(2 max r'), retried
-//     with t/4 when the CG meets non-positive curvature (M/t + H must stay
-//     positive definite) and shorter when it would move a node by more than
-//     FLOW_MOVE, and finished by Newton steps (t = infinity) once the flow
-//     has nearly arrived (see SolverParams in internal.cuh).
+//     pseudo-step t from 1/(2 max r') growing towards a move limit (at most
+//     x2 per step), retried with t/4 when the CG meets non-positive curvature
+//     (M/t + H must stay positive definite), taken shortened when it would
+//     move a node by more than FLOW_MOVE, and finished by Newton steps (t =
+//     infinity) once the flow has nearly arrived (see SolverParams in
+//     internal.cuh).
 //   * Other levels: H is positive definite for every state and the root
 //     unique; Newton with Armijo backtracking on E (sigma = 1e-4, halving, at
 //     most 40; the energy change summed node by node in a cancellation-free
@@ -264,16 +265,26 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
           tau = 0.25 * t;
           ++halvings;
         } else {
-          accept = !(dmax > FLOW_MOVE && t > FLOW_TMIN);
-          if (!accept) { tau = t * 0.5 * FLOW_MOVE / dmax; ++halvings; }
+          accept = true;
         }
         if (!accept) continue;       // the state is unchanged; retry
+        if (!newton_phase && dmax > FLOW_MOVE && t > FLOW_TMIN) {
+          // the step would move a node by more than FLOW_MOVE: take it
+          // shortened to that move (a positive multiple keeps its sign along
+          // every eigenvector of M/t + H); the next pseudo-step is shorter
+          const double sc = FLOW_MOVE / dmax;
+          for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) u[A] += sc * (double)d[A];
+          __syncthreads();
+          tau = t * 0.9 * sc;
+          ++halvings;
+          continue;
+        }
         for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) u[A] += (double)d[A];
         __syncthreads();
         if (dmax <= sp.newton_tol) { conv = true; break; }
         if (!newton_phase) {
           if (dmax <= sw) newton_phase = true;
-          tau = fmin(2.0 * t, FLOW_TMAX);
+          tau = fmin(t * fmin(2.0, 0.9 * FLOW_MOVE / dmax), FLOW_TMAX);   // towards the move limit
         }
         continue;
       }

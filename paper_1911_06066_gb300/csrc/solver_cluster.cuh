@@ -563,16 +563,26 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           tau = 0.25 * t;
           ++halvings;
         } else {
-          accept = !(dmax > FLOW_MOVE && t > FLOW_TMIN);
-          if (!accept) { tau = t * 0.5 * FLOW_MOVE / dmax; ++halvings; }
+          accept = true;
         }
         if (!accept) continue;       // the state is unchanged; retry
+        if (!newton_phase && dmax > FLOW_MOVE && t > FLOW_TMIN) {
+          // the step would move a node by more than FLOW_MOVE: take it
+          // shortened to that move (a positive multiple keeps its sign along
+          // every eigenvector of M/t + H); the next pseudo-step is shorter
+          const double sc = FLOW_MOVE / dmax;
+          for (int a = tid; a < b.nb; a += NT) u[a] += sc * (double)d[a];
+          cluster_barrier(cl, b.C);
+          tau = t * 0.9 * sc;
+          ++halvings;
+          continue;
+        }
         for (int a = tid; a < b.nb; a += NT) u[a] += (double)d[a];
         cluster_barrier(cl, b.C);
         if (dmax <= sp.newton_tol) { conv = true; break; }
         if (!newton_phase) {
           if (dmax <= sw) newton_phase = true;
-          tau = fmin(2.0 * t, FLOW_TMAX);
+          tau = fmin(t * fmin(2.0, 0.9 * FLOW_MOVE / dmax), FLOW_TMAX);   // towards the move limit
         }
         continue;
       }
