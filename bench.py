@@ -56,6 +56,9 @@ TRAFFIC_2D_BYTES_PER_SOLVE_LAUNCH = 36.85e6
 BYTES_CG32_NODE_3D = 27 * 4 + 14 * 4
 BYTES_CG64_NODE_3D = 27 * 8 + 14 * 8
 BYTES_NEWTON_NODE_3D = 2 * (27 * 8 + 8 * 8)
+# iteration cap per time step on the 3D slab: its level 1 steps take up to
+# thousands of continuation iterations
+SLAB3D_NEWTON_MAX = 40000
 
 
 def parse():
@@ -230,7 +233,8 @@ def run_ours(args, w):
         dist.init_process_group("nccl")
     prec = B.MLMC_PREC_MIXED if args.precision == "mixed" else B.MLMC_PREC_FP64
     graph = not args.no_graph
-    ctx = B.Context(B.make_config(w, prec, use_graph=graph))
+    ctx = B.Context(B.make_config(w, prec, use_graph=graph,
+                                  newton_max=SLAB3D_NEWTON_MAX if w["dim"] == 3 else 5000))
     seed = 1 + rank      # disjoint streams per rank: each rank runs its own estimate
     batch = max(w["N"])
     # a side stream: the legacy default stream cannot be captured into a graph
@@ -595,6 +599,8 @@ def run_extras(w, B, prec, seed, stream, peaks):
         "mean_correction_norm_l": d4["mean_norm"].tolist(), "weak_rate_alpha": d4["alpha"],
         "censored_fraction_l": d4["censored"].tolist(), "V_l": r4["V_l"].tolist()}
     del ctx4
+    # the paper's work model (Sec. 4.2) from this workload's measured costs
+    out["work_report"] = work_report_of(ctx, w["levels"], 32, stream)
     # ---- serving
     mix = N / N.sum()
     srv_ctx = B.Context(B.make_config(w, prec))
@@ -623,17 +629,48 @@ def run_extras(w, B, prec, seed, stream, peaks):
                                                    "batches", "failed")}
     serving["sustainable"].update({"rate": rate2, "requests": n2})
     out["serving"] = serving
-    del srv_ctx, ctx
-    # ---- the 4-level 3D slab
-    w3 = W.SLAB3D_4LVL
-    ctx3 = B.Context(B.make_config(w3, prec, use_graph=True))
-    ctx3.run([8, 4, 2, 1], seed=seed + 600, batch=8)         # warm: modules, graph shapes
+    del srv_ctx
+    # ---- the 4-level 3D slab, at reduced counts: its level 1 (64x64x16,
+    # c dt max r' = 2.37) needs thousands of continuation iterations per late
+    # step as the front widens, so the full N_l = 256/64/16/4 takes many
+    # minutes (python bench.py --workload 3d runs it)
+    w3 = dict(W.SLAB3D_4LVL, N=[16, 8, 4, 2])
+    ctx3 = B.Context(B.make_config(w3, prec, use_graph=True, newton_max=SLAB3D_NEWTON_MAX))
+    ctx3.run([2, 1, 1, 1], seed=seed + 600, batch=2)         # warm: modules, graph shapes
     r3, s3 = timed_run(ctx3, w3["N"], seed + 700, max(w3["N"]), stream)
-    lv3 = add_hbm_bytes(level_bounds(ctx3.level_stats(), 1, peaks), ctx3.level_stats(), 1)
-    out["slab3d"] = {"workload": w3["name"], "N_l": w3["N"], "grids": grids_of(w3),
+    ls3 = ctx3.level_stats()
+    lv3 = add_hbm_bytes(level_bounds(ls3, 1, peaks), ls3, 1)
+    out["slab3d"] = {"workload": W.SLAB3D_4LVL["name"], "N_l": w3["N"], "grids": grids_of(w3),
                      "seconds": s3, "rmse": r3["rmse"], "C_l": r3["C_l"].tolist(),
-                     "levels": lv3, "roofline": roofline_3d(lv3, s3 * 1e3, peaks)}
+                     "levels": lv3, "roofline": roofline_3d(lv3, s3 * 1e3, peaks),
+                     "work_report": work_report_of(ctx3, 4, 2, stream)}
     return out
+
+
+def per_sample_costs(ctx, levels, n, stream, seed=777):
+    """W'_l of Sec. 4.2: device seconds per sample of grid level l, from one
+    batch of n samples solved alone (CUDA events, after a warm-up solve)."""
+    import torch
+    out = []
+    for l in range(levels):
+        Z = ctx.kl_field(l, ctx.xi(seed, l, torch.arange(n)))
+        ctx.solve(l, Z[:1])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.solve(l, Z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1) * 1e-3 / n)
+    return out
+
+
+def work_report_of(ctx, levels, n, stream):
+    """Sec. 4.2's gamma_d (Eq. complexity) and work model (Eq. work,
+    Eq. Work-MC, Eq. Work-MLMC) from measured per-sample costs."""
+    from paper_1911_06066_gb300 import experiments as E
+    rep = E.work_report(per_sample_costs(ctx, levels, n, stream))
+    rep["how"] = "W'_l: device seconds per sample of level l, %d samples solved alone" % n
+    return rep
 
 
 def run_profile_case(args, w):
