@@ -256,13 +256,16 @@ mlmc_status mlmc_kl_tc_workspace_bytes(const mlmc_ctx* ctx, int n, size_t* bytes
  * MLMC_KL_AFFINE_GAUSSIAN, the capped scale s_eff (1 otherwise); host outputs,
  * any may be NULL. */
 mlmc_status mlmc_kl_info(const mlmc_ctx* ctx, int* rank, double* s_eff);
-/* Check of the bounded-wait path (the paper has no counterpart): with polls >=
+/* Check of the bounded-wait paths (the paper has no counterpart): with polls >=
  * 0, every tile of the context's later tensor-core KL launches first waits at
  * most `polls` polls on a barrier that nothing arms -- before it issues any
  * copy or MMA, so nothing is left in flight -- and takes its timeout exit
  * (outputs unwritten, counted; the next mlmc_run / mlmc_run_more reports
- * MLMC_ERR_TIMEOUT, and mlmc_reset clears the count).  polls = -1 restores
- * normal operation.  The device and the context stay usable throughout. */
+ * MLMC_ERR_TIMEOUT, and mlmc_reset clears the count); and the first barrier of
+ * every group-layout solve waits, at most `polls` polls, for one CTA more than
+ * the group has, so that each of its samples ends with status MLMC_ERR_TIMEOUT
+ * in its mlmc_sample_info.  polls = -1 restores normal operation.  The device
+ * and the context stay usable throughout. */
 mlmc_status mlmc_check_timeout_path(mlmc_ctx* ctx, long long polls);
 mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
                              void* ws, size_t ws_bytes, void* stream);
@@ -330,17 +333,28 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean
  * 4, 8, 16 a thread-block cluster of that many CTAs per sample with every
  * vector in shared memory (each CTA a band of whole rows; only where a band
  * fits); 100 + C (C = 1, 2, 4, 8, 16) a cluster of C CTAs per sample with the
- * vectors in global memory (each CTA a contiguous node range); 0 automatic:
- * the smallest shared-memory cluster that holds a sample, else global-memory
- * clusters of up to 16 CTAs.  Each candidate (the block kernel only with
+ * vectors in global memory (each CTA a contiguous node range);
+ * MLMC_LAYOUT_GROUP (3D grids) G CTAs per sample that are not a hardware
+ * cluster -- an ordinary grid whose CTAs form groups of G in arrival order and
+ * synchronise through bounded global-memory barriers (a wait that runs out,
+ * after 180 s, fails the sample with MLMC_ERR_TIMEOUT) -- with G = min(S/n,
+ * S/2, nodes/4096) for S resident CTAs on the device (nodes/512 when the
+ * layout is set explicitly), so that a few samples of a large grid use every
+ * SM instead of at most 16; a context runs its group
+ * launches one after another, and at most two may run at once on one device;
+ * 0 automatic: the smallest shared-memory cluster that holds a sample, else
+ * (3D) the group layout where G >= 32, else global-memory clusters of up to 16
+ * CTAs.  Each candidate (the block kernel only with
  * solver = MLMC_SOLVER_AUTO) solves the same n samples (ids device [n], drawn
  * with `seed`) once and is timed with CUDA events; the fastest becomes the
  * level's layout for every later solve of this context.
  * ws: mlmc_workspace_bytes(ctx, level, n).  Outputs (host, may be NULL): best
  * (its code) and ms [MLMC_TUNE_CANDIDATES] in the order -1, 1, 2, 4, 8, 16,
- * 101, 102, 104, 108, 116 (-1 where a candidate was not run).  Synchronises
- * the stream.  A forced cfg.cluster_size still wins over the tuned value. */
-#define MLMC_TUNE_CANDIDATES 11
+ * 101, 102, 104, 108, 116, MLMC_LAYOUT_GROUP (-1 where a candidate was not
+ * run).  Synchronises the stream.  A forced cfg.cluster_size still wins over
+ * the tuned value. */
+#define MLMC_TUNE_CANDIDATES 12
+#define MLMC_LAYOUT_GROUP 200
 mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* ids, int n,
                           void* ws, size_t ws_bytes, int* best, float* ms, void* stream);
 /* The layout code used for a level, and a way to set it without tuning (e.g.

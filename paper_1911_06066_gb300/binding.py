@@ -41,6 +41,7 @@ class mlmc_config(C.Structure):
 
 MLMC_SOLVER_AUTO, MLMC_SOLVER_BLOCK, MLMC_SOLVER_CLUSTER = 0, 1, 2
 MLMC_PRECOND_JACOBI, MLMC_PRECOND_GMG = 0, 1
+MLMC_LAYOUT_GROUP = 200
 MLMC_SCHEME_IE, MLMC_SCHEME_CN = 0, 1
 MLMC_STIM_BALL, MLMC_STIM_PULSE = 0, 1
 MLMC_QOI_ACTIVATION, MLMC_QOI_FINAL_STATE = 0, 1
@@ -497,7 +498,9 @@ class Context:
 
     def check_timeout_path(self, polls):
         """polls >= 0: the tensor-core KL tiles time out on purpose (before
-        issuing any work); -1: normal operation (mlmc_check_timeout_path)."""
+        issuing any work) and the group-layout solves' first barrier waits for
+        one CTA too many (every sample reports MLMC_ERR_TIMEOUT); -1: normal
+        operation (mlmc_check_timeout_path)."""
         self._check(lib().mlmc_check_timeout_path(self.h, int(polls)))
 
     def level_stats(self):
@@ -526,10 +529,10 @@ class Context:
         ids = torch.arange(first_id, first_id + n, dtype=torch.int64, device="cuda")
         ws = self.workspace(self.workspace_bytes(level, n), key="tune")
         best = C.c_int()
-        ms = np.zeros(11, np.float32)
+        ms = np.zeros(12, np.float32)
         self._check(lib().mlmc_autotune(self.h, level, seed, _p(ids), n, _p(ws), ws.numel(),
                                         C.byref(best), _dp(ms), _stream(stream)))
-        names = (-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116)
+        names = (-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116, MLMC_LAYOUT_GROUP)
         return best.value, {k: float(v) for k, v in zip(names, ms) if v >= 0}
 
     def layout(self, level):

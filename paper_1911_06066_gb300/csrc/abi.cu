@@ -82,6 +82,10 @@ SolveWs mlmc::solve_ws(const mlmc_config& c, const LevelDesc& lv, int n, bool mi
   w.Kd = off; off += align256((size_t)n * N * 8);
   w.kr = off; off += align256((size_t)n * 7 * N * kr);
   w.mg = off; off += align256((size_t)n * (size_t)mg.per_sample * kr);
+  // group layout (global-memory levels): tickets, barrier counters, partials
+  w.grp = off;
+  if (lv.dim == 3)
+    off += align256(group_sync_bytes(GROUP_MAX_SAMPLES)) + align256((size_t)16 * GROUP_MAX_GRID * 8);
   w.total = off;
   return w;
 }
@@ -347,6 +351,7 @@ extern "C" void mlmc_destroy(mlmc_ctx* ctx) {
   cudaFree(ctx->d_est);
   cudaFree(ctx->d_cnt);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->grp_ev) cudaEventDestroy(ctx->grp_ev);
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
   for (cudaEvent_t ev : ctx->sync_pool) cudaEventDestroy(ev);
   for (int i = 0; i < 2 * MLMC_MAX_LEVELS; ++i)
@@ -462,26 +467,34 @@ static mlmc_status kl_into(mlmc_ctx* ctx, int level, const double* xi, int n, do
 
 // Coefficients + sweep for n samples of one level inside an already checked
 // workspace region.
-// The solve layout of a level: false = the block-per-sample kernel, else a
-// cluster plan.  Layout codes (mlmc_set_layout): -1 block kernel, 0 automatic
-// (the smallest shared-memory cluster that holds a sample, else global-memory
-// clusters), 1..16 shared-memory clusters of that size, 100 + C global-memory
-// clusters of C CTAs.
-static bool choose_plan(const mlmc_ctx* ctx, const LevelDesc& lv, bool mixed, int level,
+// The solve layout of a level for a launch of n samples: false = the
+// block-per-sample kernel, else a cluster or group plan.  Layout codes
+// (mlmc_set_layout): -1 block kernel, 0 automatic (the smallest shared-memory
+// cluster that holds a sample; else, on 3D grids, the group layout when it
+// gives a sample at least 32 CTAs; else global-memory clusters of 16), 1..16
+// shared-memory clusters of that size, 100 + C global-memory clusters of C
+// CTAs, MLMC_LAYOUT_GROUP the group layout.
+static bool choose_plan(const mlmc_ctx* ctx, const LevelDesc& lv, bool mixed, int level, int n,
                         ClusterPlan* plan) {
   if (ctx->cfg.solver == MLMC_SOLVER_BLOCK) return false;
   const int want = ctx->cfg.cluster_size ? ctx->cfg.cluster_size : ctx->tuned_C[level];
   if (want < 0 && ctx->cfg.solver == MLMC_SOLVER_AUTO) return false;
+  bool ok = false;
+  if (want == MLMC_LAYOUT_GROUP) {
+    if (group_plan(lv, mixed, n, true, plan, &ok) == cudaSuccess && ok) return true;
+    return cluster_plan(lv, mixed, 0, plan, true);
+  }
   if (want > 100) return cluster_plan(lv, mixed, want - 100, plan, true);
   if (want > 0 && cluster_plan(lv, mixed, want, plan)) return true;
   MGDesc mg;
   if (want == 0 && level_gmg(ctx->cfg, lv, &mg)) return cluster_plan(lv, mixed, 0, plan, true);
   if (cluster_plan(lv, mixed, 0, plan)) return true;
+  if (want == 0 && group_plan(lv, mixed, n, false, plan, &ok) == cudaSuccess && ok) return true;
   return cluster_plan(lv, mixed, 0, plan, true);
 }
 
 static bool valid_layout(int C) {
-  const int ok[12] = {-1, 0, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116};
+  const int ok[13] = {-1, 0, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116, MLMC_LAYOUT_GROUP};
   for (int v : ok)
     if (C == v) return true;
   return false;
@@ -499,7 +512,7 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
   float* coef32 = mixed ? (float*)(ws + w.coef32) : nullptr;
   CK(ctx, launch_assemble(lv, ph, Z, n, coef64, coef32, st));
   ClusterPlan plan;
-  const bool use_cluster = choose_plan(ctx, lv, mixed, level, &plan);
+  const bool use_cluster = choose_plan(ctx, lv, mixed, level, n, &plan);
   if (ctx->cfg.solver == MLMC_SOLVER_CLUSTER && !use_cluster)
     return fail(ctx, MLMC_ERR_ARG, "cluster layout requested but no cluster plan fits");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -515,7 +528,8 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     ctx->ev_grid.push_back(level);
     CK(ctx, cudaEventRecordWithFlags(e0, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  const SolverParams sp = level_solver_params(ctx->cfg, lv, mixed);
+  SolverParams sp = level_solver_params(ctx->cfg, lv, mixed);
+  sp.grp_check = ctx->tc_check_limit;
   if (use_cluster) {
     ClusterGlobal g;
     g.u = (double*)(ws + w.ubuf);
@@ -525,8 +539,19 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     MGDesc mg;
     level_gmg(ctx->cfg, lv, &mg);
     g.mg = mg.G > 0 ? (void*)(ws + w.mg) : nullptr;
+    if (plan.G > 0) {
+      g.gsync = (unsigned*)(ws + w.grp);
+      g.gslot = (double*)(ws + w.grp + align256(group_sync_bytes(GROUP_MAX_SAMPLES)));
+      // group launches of this context run one after another
+      if (ctx->grp_ev_valid) CK(ctx, cudaStreamWaitEvent(st, ctx->grp_ev, 0));
+    }
     CK(ctx, launch_solve_cluster(lv, ph, sp, mixed, plan, n, coef64, coef32, slab, t_act, info,
                                  ctx->d_cnt + CNT_LEVEL + CNT_PER_LEVEL * level, g, mg, st));
+    if (plan.G > 0) {
+      if (!ctx->grp_ev) CK(ctx, cudaEventCreateWithFlags(&ctx->grp_ev, cudaEventDisableTiming));
+      CK(ctx, cudaEventRecord(ctx->grp_ev, st));
+      ctx->grp_ev_valid = true;
+    }
   }
   else
     CK(ctx, launch_solve(lv, ph, sp, mixed, n, coef64, coef32, slab, (double*)(ws + w.ubuf),
@@ -576,7 +601,8 @@ extern "C" mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, co
   if ((r = mlmc_kl_field(ctx, level, xi, n, Z, st)) != MLMC_OK) return r;
   // candidates: the block kernel (only when the layout is not forced), shared-
   // memory clusters of 1..16 CTAs (where a band fits), global-memory clusters
-  const int cand[MLMC_TUNE_CANDIDATES] = {-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116};
+  const int cand[MLMC_TUNE_CANDIDATES] = {-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116,
+                                          MLMC_LAYOUT_GROUP};
   float t_ms[MLMC_TUNE_CANDIDATES];
   int choice = 0;
   float best_ms = 0.f;
@@ -598,7 +624,13 @@ extern "C" mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, co
     if (C > 0) {
       ClusterPlan pl;
       if (ctx->cfg.solver == MLMC_SOLVER_BLOCK) continue;
-      if (!cluster_plan(lv, mixed, C > 100 ? C - 100 : C, &pl, C > 100)) continue;
+      if (C == MLMC_LAYOUT_GROUP) {
+        bool gok = false;
+        CK(ctx, group_plan(lv, mixed, n, true, &pl, &gok));
+        if (!gok) continue;
+      } else if (!cluster_plan(lv, mixed, C > 100 ? C - 100 : C, &pl, C > 100)) {
+        continue;
+      }
       int active = 0;
       CK(ctx, cluster_max_active(lv, mixed, pl, &active));
       if (active < 1) continue;
@@ -830,16 +862,23 @@ static mlmc_status run_levels(mlmc_ctx* ctx, const int64_t* first_id, const int6
         const LevelDesc& d = ctx->lv[lv];
         const bool mx = level_mixed(ctx->cfg, d);
         ClusterPlan pl;
-        if (choose_plan(ctx, d, mx, lv, &pl)) CK(ctx, preload_solve_cluster(d, mx, pl));
-        else CK(ctx, preload_solve(d, mx));
+        if (choose_plan(ctx, d, mx, lv, level_batch(count[l], batch), &pl))
+          CK(ctx, preload_solve_cluster(d, mx, pl));
+        else
+          CK(ctx, preload_solve(d, mx));
+        bool gok = false;   // any batch size may pick the group layout on 3D grids
+        if (d.dim == 3 && group_plan(d, mx, 1, true, &pl, &gok) == cudaSuccess && gok)
+          CK(ctx, preload_solve_cluster(d, mx, pl));
       }
     }
     CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     ctx->capturing = true;
+    ctx->grp_ev_valid = false;   // no waits on events recorded outside the capture
   }
   r = enqueue_levels(ctx, first_id, count, seed, batch, ws, st);
   if (graph) {
     ctx->capturing = false;
+    ctx->grp_ev_valid = false;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
     if (r != MLMC_OK) {

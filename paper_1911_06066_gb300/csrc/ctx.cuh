@@ -55,6 +55,12 @@ struct mlmc_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   long graph_runs = 0;
   long long tc_check_limit = -1;   // mlmc_check_timeout_path: -1 normal operation
+  // group-layout solves of one context run one after another (each waits for
+  // the previous one): grp_ev is recorded after every group launch and is
+  // valid for the next one while grp_ev_valid holds (reset at the start and
+  // end of a graph capture, whose events cannot be waited on across it)
+  cudaEvent_t grp_ev = nullptr;
+  bool grp_ev_valid = false;
   std::string err;
 };
 

@@ -65,6 +65,9 @@ struct SolverParams {
                          // gradient-flow continuation instead of Newton-CG
   double tau0;           // first pseudo-step of the continuation, 1 / (2 max r')
   int cg_scale;          // FP32 CG: solve for a power-of-two scaled right-hand side
+  long long grp_check = -1;   // >= 0: check of the group layout's bounded waits -- the
+                              // first barrier waits for one arrival too many, at most
+                              // grp_check polls, and the sample ends with MLMC_ERR_TIMEOUT
 };
 
 // Gradient-flow continuation (levels with c dt max r' > 1; max r' =
@@ -102,7 +105,7 @@ SolverParams level_solver_params(const mlmc_config& c, const LevelDesc& lv, bool
 // Byte offsets of one level's solver scratch for n samples (the workspace of
 // mlmc_solve), 256-byte aligned.
 struct SolveWs {
-  size_t coef64, coef32, ubuf, F, Ku, Kd, kr, mg, total;
+  size_t coef64, coef32, ubuf, F, Ku, Kd, kr, mg, grp, total;
 };
 SolveWs solve_ws(const mlmc_config& c, const LevelDesc& lv, int n, bool mixed);
 
@@ -233,7 +236,18 @@ struct ClusterPlan {
   bool coef_smem;
   bool gm;        // vectors in global memory (H = nodes per CTA), else shared (H = rows per CTA)
   size_t smem;
+  int G = 0;      // > 0: the group layout -- gm vectors, C = G CTAs per sample as a plain grid
 };
+// Group layout: per launch a ticket counter and per sample an arrival counter
+// and a give-up flag (128 bytes apart), and the reductions' CTA partials
+// [2][8][G] per sample.  GROUP_MAX_CTAS bounds G; the group area of a solve
+// workspace holds GROUP_MAX_SAMPLES samples (launches with more samples use
+// the cluster layouts).
+constexpr int GROUP_MAX_CTAS = 1024;
+constexpr int GROUP_MAX_SAMPLES = 64;
+constexpr int GROUP_MAX_GRID = 4096;   // bound on samples x G of one launch
+inline size_t group_sync_bytes(int n) { return (size_t)32 * 4 * (size_t)(n + 1); }
+inline size_t group_slot_bytes(int n, int G) { return (size_t)n * 16 * (size_t)G * 8; }
 // Global-memory vectors of the gm layout, per sample: u [2N], F [N] (FP64),
 // r z p q d diag diag^-1 [7N] in the CG's precision, node codes [N].
 struct ClusterGlobal {
@@ -242,8 +256,19 @@ struct ClusterGlobal {
   void* kr = nullptr;
   unsigned* code = nullptr;
   void* mg = nullptr;     // multigrid workspace (MGDesc::per_sample elements per sample), or NULL
+  unsigned* gsync = nullptr;   // group layout: group_sync_bytes(n)
+  double* gslot = nullptr;     // group layout: group_slot_bytes(n, G)
 };
 bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm = false);
+// Group layout plan for n samples of the 3D grid lv: G CTAs per sample with
+// G = min(S / n, S / 2, GROUP_MAX_CTAS, nodes / 4096, GROUP_MAX_GRID / n), S
+// the device's resident-CTA capacity for the group kernel (force, the layout
+// requested by code: nodes / 512 instead of nodes / 4096).  *ok = false when
+// the layout does not apply: not 3D, n above GROUP_MAX_SAMPLES, or G below 32
+// (below 1 with force), where clusters of 16 CTAs serve as well.  G <= S / 2
+// keeps two group launches running at once (e.g. from two contexts) free of
+// deadlock: each waits at most for one incomplete group of its own.
+cudaError_t group_plan(const LevelDesc& lv, bool mixed, int n, bool force, ClusterPlan* plan, bool* ok);
 size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt);
 // Loads the kernel instance a plan launches and sets its attributes, so that
 // a timed launch does not include module loading.

@@ -61,6 +61,11 @@ static cudaError_t launch_nt(const LevelDesc& lv, const Physics& ph, const Solve
                              double* slab, double* t_act, mlmc_sample_info* info,
                              unsigned long long* counters, const ClusterGlobal& g,
                              const MGDesc& mg, cudaStream_t st) {
+  if (pl.G > 0) {
+    if (DIM != 3) return cudaErrorInvalidValue;   // the group layout serves the 3D grids
+    return launch_one<KR, 3, true, false, true>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info,
+                                                counters, g, mg, st);
+  }
   if (pl.gm)
     return launch_one<KR, DIM, true, false>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info,
                                             counters, g, mg, st);
@@ -70,7 +75,55 @@ static cudaError_t launch_nt(const LevelDesc& lv, const Physics& ph, const Solve
 
 template <typename KR, int DIM>
 static cudaError_t preload_one(const ClusterPlan& pl) {
+  if (pl.G > 0) return set_attrs<KR, 3, true, false, true>(pl);
   return pl.gm ? set_attrs<KR, DIM, true>(pl) : set_attrs<KR, DIM, false>(pl);
+}
+
+// Resident CTAs of the group kernel on the current device (per SM x SMs),
+// cached per device and precision: the first query loads the kernel, so it
+// runs before any graph capture (group_plan is called from the preloads).
+template <typename KR>
+static cudaError_t group_slots(size_t smem, int* S) {
+  static int cache[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && cache[dev] > 0) {
+    *S = cache[dev];
+    return cudaSuccess;
+  }
+  int sms = 0, per = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  auto kern = solve_cluster_kernel<KR, 3, 512, 5, true, false, true>;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 512, smem)) != cudaSuccess) return e;
+  *S = per * sms;
+  if (dev >= 0 && dev < 64) cache[dev] = *S;
+  return cudaSuccess;
+}
+
+cudaError_t group_plan(const LevelDesc& lv, bool mixed, int n, bool force, ClusterPlan* plan, bool* ok) {
+  *ok = false;
+  if (lv.dim != 3 || n < 1 || n > GROUP_MAX_SAMPLES) return cudaSuccess;
+  ClusterPlan pl;
+  if (!cluster_plan(lv, mixed, 16, &pl, true)) return cudaSuccess;
+  int S = 0;
+  cudaError_t e = mixed ? group_slots<float>(pl.smem, &S) : group_slots<double>(pl.smem, &S);
+  if (e != cudaSuccess) return e;
+  int G = S / n;
+  if (G > S / 2) G = S / 2;
+  if (G > GROUP_MAX_CTAS) G = GROUP_MAX_CTAS;
+  const int64_t per_cta = force ? 512 : 4096;   // nodes per CTA at least
+  if ((int64_t)G > lv.nodes / per_cta) G = (int)(lv.nodes / per_cta);
+  if ((int64_t)n * G > GROUP_MAX_GRID) G = GROUP_MAX_GRID / n;
+  if (G < (force ? 1 : 32)) return cudaSuccess;
+  pl.C = G;
+  pl.G = G;
+  pl.H = (int)((lv.nodes + G - 1) / G);
+  *plan = pl;
+  *ok = true;
+  return cudaSuccess;
 }
 
 template <typename KR, int DIM>
@@ -79,6 +132,13 @@ static cudaError_t max_clusters_one(const ClusterPlan& pl, int* count) {
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t cfg = launch_cfg(pl, 1, nullptr, at);
+  if (pl.G > 0) {   // the group layout needs every CTA resident: one group
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_cluster_kernel<KR, 3, 512, 5, true, false, true>,
+                                                      512, pl.smem);
+    *count = per > 0 ? 1 : 0;
+    return e;
+  }
   return pl.gm ? cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, true, false>, &cfg)
                : cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, false, false>, &cfg);
 }
@@ -108,6 +168,9 @@ cudaError_t launch_solve_cluster(const LevelDesc& lv, const Physics& ph, const S
                                  const ClusterGlobal& g, const MGDesc& mg, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   if (pl.gm && (!g.u || !g.F || !g.kr || !g.code)) return cudaErrorInvalidValue;
+  if (pl.G > 0 && (!g.gsync || !g.gslot || mg.G > 0 || n > GROUP_MAX_SAMPLES ||
+                   (int64_t)n * pl.G > GROUP_MAX_GRID))
+    return cudaErrorInvalidValue;
   if (pl.gm && mg.G > 0) {
     if (!g.mg || mg.nu < 1 || mg.coarse_sweeps < 1 || mg.G > MG_MAX_LEVELS) return cudaErrorInvalidValue;
     return launch_solve_cluster_gmg(lv, ph, sp, mixed, pl, n, coef64, coef32, slab, t_act, info,

@@ -15,7 +15,8 @@
 // needs anyway.  Dot products are reduced per warp, per CTA (fixed order),
 // then across the cluster by reading every CTA's partial in rank order, so the
 // result is identical on all CTAs and deterministic.  Per CG iteration the
-// cluster synchronises three times (p^T H p, r^T z, and the new p).
+// cluster synchronises twice (p^T H p and r^T z): the new search direction
+// is formed inside the next stencil pass.
 //
 // Only the per-sample couplings (read once per Newton step by the residual)
 // and the outputs stay in global memory.
@@ -118,6 +119,75 @@ __device__ __forceinline__ TA stencil_fast(const TV* v, int a, int N0, int N01, 
   return y;
 }
 
+// Synchronisation of the group layout (GRP): the G CTAs of one sample are
+// not a hardware cluster but CTAs of an ordinary grid that took consecutive
+// tickets on arrival (so a group only ever waits for CTAs that are already
+// resident).  A barrier is a monotonic arrival counter in global memory:
+// every CTA adds one and waits until the counter reaches G times the number
+// of barriers passed.  Thread 0 publishes the CTA's writes with a gpu-scope
+// fence before arriving and acquires the others' after the wait, between two
+// CTA barriers -- the order in which grid-wide barriers are built.  A wait is
+// bounded (GROUP_WAIT_NS of global time); a CTA whose wait runs out raises
+// the sample's give-up flag, which ends every other wait of the sample at
+// once, and the kernel reports MLMC_ERR_TIMEOUT for the sample.
+constexpr unsigned long long GROUP_WAIT_NS = 180ull * 1000000000ull;
+
+struct GroupSync {
+  unsigned* ctr = nullptr;    // arrivals of the sample's CTAs
+  unsigned* flag = nullptr;   // give-up flag of the sample
+  double* slot = nullptr;     // reduction partials [2][8][G]
+  unsigned target = 0;        // arrivals that complete the next barrier
+  int* abort = nullptr;       // shared: this CTA gave up
+  long long check = -1;       // >= 0: wait for one arrival more, at most check polls
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __noinline__ void group_barrier(GroupSync& gs, int G) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gs.target += (unsigned)G;
+    __threadfence();
+    atomicAdd(gs.ctr, 1u);
+    if (*gs.abort == 0) {
+      const unsigned long long t0 = global_ns();
+      const unsigned want = gs.target + (gs.check >= 0 ? 1u : 0u);   // the check never arrives
+      long long polls = 0;
+      while ((int)(ld_acquire_gpu(gs.ctr) - want) < 0) {
+        ++polls;
+        if (ld_acquire_gpu(gs.flag) != 0u || (gs.check >= 0 && polls > gs.check) ||
+            ((polls & 255) == 0 && global_ns() - t0 > GROUP_WAIT_NS)) {
+          *gs.abort = 1;
+          atomicExch(gs.flag, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl, int C) {
+  if (C == 1) __syncthreads(); else cl.sync();
+}
+
+template <bool GRP>
+__device__ __forceinline__ void sync_all(cg::cluster_group& cl, int C, GroupSync& gs) {
+  if (GRP) group_barrier(gs, C);
+  else cluster_barrier(cl, C);
+}
+
 // Deterministic cluster-wide sums (op 0) or maxima (op 1, of non-negative
 // values) of K values per thread.  Warps reduce by butterfly shuffles in TP
 // (float in the mixed CG, double otherwise); warp 0 combines the CTA's warps
@@ -130,10 +200,10 @@ __device__ __forceinline__ TA stencil_fast(const TV* v, int a, int N0, int N01, 
 template <typename TP>
 __device__ __forceinline__ TP combine(TP x, TP y, int op) { return op ? (x > y ? x : y) : x + y; }
 
-template <int NT, typename TP, int K, typename POST>
+template <int NT, typename TP, int K, bool GRP, typename POST>
 __device__ __forceinline__ void cluster_reduce(TP (&v)[K], int op, double* red, double* slot,
                                                double* bc, int& par, cg::cluster_group& cl, int C,
-                                               int rank, POST post) {
+                                               int rank, GroupSync& gs, POST post) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -150,7 +220,12 @@ __device__ __forceinline__ void cluster_reduce(TP (&v)[K], int op, double* red, 
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t[k] = combine(t[k], __shfl_xor_sync(0xffffffffu, t[k], o), op);
     }
-    if (C == 1) {
+    if (GRP) {
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) gs.slot[(par * 8 + k) * C + rank] = (double)t[k];
+      }
+    } else if (C == 1) {
       if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) bc[k] = (double)t[k];
@@ -162,7 +237,27 @@ __device__ __forceinline__ void cluster_reduce(TP (&v)[K], int op, double* red, 
       for (int k = 0; k < K; ++k) dst[k * 16] = (double)t[k];
     }
   }
-  if (C > 1) {
+  if (GRP) {
+    // every CTA combines the G partials in the same fixed order: lane q sums
+    // the partials q, q + 32, ... (read from L2), then the butterfly tree
+    group_barrier(gs, C);
+    if (warp == 0) {
+      TP t[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        t[k] = (TP)0;
+        for (int q = lane; q < C; q += 32)
+          t[k] = combine(t[k], (TP)__ldcg(gs.slot + (par * 8 + k) * C + q), op);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t[k] = combine(t[k], __shfl_xor_sync(0xffffffffu, t[k], o), op);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) bc[k] = (double)t[k];
+        post(bc);
+      }
+    }
+  } else if (C > 1) {
     cl.sync();
     if (warp == 0) {
       TP t[K];
@@ -202,10 +297,6 @@ __device__ __forceinline__ unsigned gm_code(const Band& b, int A) {
   return (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22) | (in ? 0x80000000u : 0u);
 }
 
-__device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl, int C) {
-  if (C == 1) __syncthreads(); else cl.sync();
-}
-
 }  // namespace
 
 // Byte offsets of the per-CTA shared-memory arrays; every array starts on a
@@ -239,25 +330,46 @@ __host__ __device__ inline SmemLayout smem_layout(int dim, int nmax, int kr, boo
 // compiled for two CTAs per SM (64 registers; the Newton and line-search
 // phases spill a few words), which doubles the warps in flight on the CG
 // passes -- 1.5-1.8x faster on the 3D levels than one CTA with 128 registers.
-template <typename KR, int DIM, int NT, int NPT, bool GM, bool MG>
+template <typename KR, int DIM, int NT, int NPT, bool GM, bool MG, bool GRP = false>
 __global__ void __launch_bounds__(NT, GM ? 2 : 1)
 solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict__ coef64,
                      const KR* __restrict__ coefK, int H, int coef_smem, double* slab,
                      double* t_act, mlmc_sample_info* info, unsigned long long* counters,
                      double* g_u, double* g_F, KR* g_kr, unsigned* g_code, const MGDesc mg,
-                     KR* g_mg) {
+                     KR* g_mg, int G, unsigned* g_sync, double* g_slot) {
   static_assert(!MG || GM, "the multigrid preconditioner needs the global-memory layout");
+  static_assert(!GRP || (GM && !MG), "the group layout is the global-memory layout with Jacobi");
   constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
   constexpr int CTR = DIM == 3 ? 13 : (DIM == 2 ? 4 : 1);
   cg::cluster_group cl = cg::this_cluster();
   Band b;
-  b.C = (int)cl.num_blocks();
-  b.rank = (int)cl.block_rank();
+  __shared__ int s_ticket, s_abort;
+  GroupSync gs;
+  int s;
+  if (GRP) {
+    // group layout: sample s = ticket / G, rank = ticket % G in arrival order
+    if (threadIdx.x == 0) {
+      s_ticket = (int)atomicAdd(g_sync, 1u);
+      s_abort = 0;
+    }
+    __syncthreads();
+    b.C = G;
+    b.rank = s_ticket % G;
+    s = s_ticket / G;
+    gs.ctr = g_sync + 32 * (s + 1);
+    gs.flag = gs.ctr + 1;
+    gs.slot = g_slot + (int64_t)s * 16 * G;
+    gs.abort = &s_abort;
+    gs.check = sp.grp_check;
+  } else {
+    b.C = (int)cl.num_blocks();
+    b.rank = (int)cl.block_rank();
+    s = blockIdx.x / b.C;
+  }
   b.N0 = lv.N[0]; b.N1 = lv.N[1]; b.N2 = lv.N[2];
   b.rowlen = DIM == 3 ? b.N0 * b.N1 : b.N0;
   b.nrows = DIM == 3 ? b.N2 : b.N1;
   b.H = H;
-  const int s = blockIdx.x / b.C;
   const int N = (int)lv.nodes;
   if (GM) {
     // H nodes per CTA, contiguous
@@ -330,7 +442,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
 #define CK_(c) ((int)(((c) >> 22) & 511u))
 #define CFAST(c) (((c) & 0x80000000u) != 0u)
 
-  cl.sync();   // every CTA of the cluster is resident before any DSMEM access
+  if (!GRP) cl.sync();   // every CTA of the cluster is resident before any DSMEM access
 
   KR* const mgb = MG ? g_mg + (int64_t)s * mg.per_sample : nullptr;
   if (MG) gmg::build<NT, DIM, KR>(mg, mgb, coef64 + (int64_t)s * NO * N, cl, b.C, b.rank);
@@ -352,6 +464,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     if (sl) sl[A] = v;
   }
   const View<KR> pv = make_view<GM>(cl, b, p);
+  const View<KR> zview = make_view<GM>(cl, b, z);
   const View<KR> dv = make_view<GM>(cl, b, d);
   const View<double> uv0 = make_view<GM>(cl, b, ubuf0);
   const View<double> uv1 = make_view<GM>(cl, b, ubuf1);
@@ -369,7 +482,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     const double c_up = (1.0 - ph.theta) / ph.theta;
     const double src_scale = stim_step_scale(ph, step, dt);
     for (int a = tid; a < b.nb; a += NT) u[a] = up[a];
-    cluster_barrier(cl, b.C);
+    sync_all<GRP>(cl, b.C, gs);
     // On levels whose steps have several roots (sp.flow) the step follows the
     // gradient-flow continuation (see SolverParams).
     double tau = sp.tau0, sw = FLOW_NEWTON;
@@ -377,6 +490,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     bool conv = false, lin_fail = false;
     int it;
     for (it = 1; it <= sp.newton_max; ++it) {
+      if (GRP && s_abort) break;   // a group wait ran out: stop
       // pseudo-step of the continuation (shift = M/t on the Hessian diagonal),
       // or a Newton step (shift 0)
       const double t = tau;
@@ -433,7 +547,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       double sigma = 1.0, rz_scaled = 0.0;
       if (SCALE) {
         double v2[2] = {f2_loc, f2p_loc};
-        cluster_reduce<NT, double, 2>(v2, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+        cluster_reduce<NT, double, 2, GRP>(v2, 0, red, slot, bc, par, cl, b.C, b.rank, gs, NoPost());
         if (bc[0] > 0.0) sigma = ldexp(1.0, -ilogb(sqrt(bc[0])));
         rz_scaled = bc[1] * sigma * sigma;
         for (int a = tid; a < b.nb; a += NT) {
@@ -444,10 +558,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
             z[a] = zv; p[a] = zv;
           }
         }
-        if (!MG) cluster_barrier(cl, b.C);   // p is read across the cluster next
+        if (!MG) sync_all<GRP>(cl, b.C, gs);   // p is read across the cluster next
       }
       if (MG) {
-        cluster_barrier(cl, b.C);
+        sync_all<GRP>(cl, b.C, gs);
         gmg::newton_setup<NT, DIM, KR>(mg, mgb, hm - base, cl, b.C, b.rank);
         gmg::vcycle<NT, DIM, KR>(mg, mgb, cKg, hm - base, pinv - base, r - base, z - base, cl, b.C,
                                  b.rank);
@@ -459,7 +573,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       }
       if (MG || !SCALE) {
         KR v1[1] = {rz_loc};
-        cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+        cluster_reduce<NT, KR, 1, GRP>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, gs, NoPost());
       }
       double rz = MG || !SCALE ? bc[0] : rz_scaled;
       const double rz_stop = rtol2 * rz;
@@ -467,34 +581,52 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       bool truncated = false;
       if (rz > 0.0) {
         bool ok = false;
+        // From the second iteration on, the search direction p = z + beta p
+        // and q = H p are formed in the same pass as the stencil, from
+        // H p = H z + beta q (the stencil is applied to z, which the last
+        // reduction's cluster barrier published): no separate pass and
+        // cluster barrier for the new p.
+        KR beta_prev = 0;
         for (cgi = 1; cgi <= sp.lin_max; ++cgi) {
           KR pq_loc = 0;
+          const bool first = cgi == 1;
+          const KR* sv = first ? p : z;               // the vector the stencil reads
+          const View<KR>& svv = first ? pv : zview;
           for (int a = tid; a < b.nb; a += NT) {
             const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
             const int A = base + a;
-            KR hp;
+            KR hs;
             if (!GM && coef_smem) {
               auto cf = [=](int o) { return cs[o * nmax + a]; };
-              hp = CFAST(c) ? stencil_fast<DIM, KR>(p, a, b.N0, N01, cf)
-                            : stencil_band<DIM, GM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
+              hs = CFAST(c) ? stencil_fast<DIM, KR>(sv, a, b.N0, N01, cf)
+                            : stencil_band<DIM, GM, KR>(b, svv, CI(c), CJ(c), CK_(c), cf);
             } else {
               auto cf = [=](int o) { return cKg[(int64_t)o * N + A]; };
-              hp = CFAST(c) ? stencil_fast<DIM, KR>(p, a, b.N0, N01, cf)
-                            : stencil_band<DIM, GM, KR>(b, pv, CI(c), CJ(c), CK_(c), cf);
+              hs = CFAST(c) ? stencil_fast<DIM, KR>(sv, a, b.N0, N01, cf)
+                            : stencil_band<DIM, GM, KR>(b, svv, CI(c), CJ(c), CK_(c), cf);
             }
-            const KR pa = p[a];
-            const KR qv = hp + hm[a] * pa;
+            const KR sa = sv[a];
+            KR pa, qv;
+            if (first) {
+              pa = sa;
+              qv = hs + hm[a] * sa;
+            } else {
+              pa = sa + beta_prev * p[a];
+              qv = (hs + hm[a] * sa) + beta_prev * q[a];
+              p[a] = pa;
+            }
             q[a] = qv;
             pq_loc += pa * qv;
           }
           const double rzc = rz;
           {
             KR v1[1] = {pq_loc};
-            cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, [=](double* o) {
+            cluster_reduce<NT, KR, 1, GRP>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, gs, [=](double* o) {
               o[1] = o[0] > 0.0 ? (double)((KR)rzc / (KR)o[0]) : 0.0;
             });
           }
           const double pq = bc[0];
+          if (GRP && s_abort) break;
           if (pq <= 0.0) {
             truncated = true;
             if (cgi == 1)
@@ -509,7 +641,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
               d[a] += alpha * p[a];
               r[a] = r[a] - alpha * q[a];
             }
-            cluster_barrier(cl, b.C);
+            sync_all<GRP>(cl, b.C, gs);
             gmg::vcycle<NT, DIM, KR>(mg, mgb, cKg, hm - base, pinv - base, r - base, z - base, cl,
                                      b.C, b.rank);
             for (int a = tid; a < b.nb; a += NT) rzn_loc += r[a] * z[a];
@@ -525,16 +657,15 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           }
           {
             KR v1[1] = {rzn_loc};
-            cluster_reduce<NT, KR, 1>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, [=](double* o) {
+            cluster_reduce<NT, KR, 1, GRP>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, gs, [=](double* o) {
               o[1] = (double)((KR)o[0] / (KR)rzc);
               o[2] = o[0] <= rz_stop ? 1.0 : 0.0;
             });
           }
           const double rz_new = bc[0];
+          if (GRP && s_abort) break;
           if (bc[2] != 0.0) { ok = true; break; }
-          const KR beta = (KR)bc[1];
-          for (int a = tid; a < b.nb; a += NT) p[a] = z[a] + beta * p[a];
-          cluster_barrier(cl, b.C);
+          beta_prev = (KR)bc[1];
           rz = rz_new;
         }
         if (!ok) { lin_fail = true; cgi = sp.lin_max; }
@@ -550,7 +681,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       for (int a = tid; a < b.nb; a += NT) dm_loc = fmax(dm_loc, fabs(d[a]));   // exact in KR
       {
         KR v1[1] = {dm_loc};
-        cluster_reduce<NT, KR, 1>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, NoPost());
+        cluster_reduce<NT, KR, 1, GRP>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, gs, NoPost());
       }
       const double dmax = bc[0];
       if (sp.flow) {
@@ -572,13 +703,13 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           // every eigenvector of M/t + H); the next pseudo-step is shorter
           const double sc = FLOW_MOVE / dmax;
           for (int a = tid; a < b.nb; a += NT) u[a] += sc * (double)d[a];
-          cluster_barrier(cl, b.C);
+          sync_all<GRP>(cl, b.C, gs);
           tau = t * 0.9 * sc;
           ++halvings;
           continue;
         }
         for (int a = tid; a < b.nb; a += NT) u[a] += (double)d[a];
-        cluster_barrier(cl, b.C);
+        sync_all<GRP>(cl, b.C, gs);
         if (dmax <= sp.newton_tol) { conv = true; break; }
         if (!newton_phase) {
           if (dmax <= sw) newton_phase = true;
@@ -611,7 +742,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           v4[3] += mA * d2 * d2;
         }
         const double alpha0 = alpha, cc = ph.c;   // alpha0 = 1
-        cluster_reduce<NT, double, 4>(v4, 0, red, slot, bc, par, cl, b.C, b.rank,
+        cluster_reduce<NT, double, 4, GRP>(v4, 0, red, slot, bc, par, cl, b.C, b.rank, gs,
                                       [=](double* o) {
                                         const double gd = o[0], dHd = o[1];
                                         const double P3 = o[2] / 6.0, P4 = -6.0 * cc * o[3] / 24.0;
@@ -630,13 +761,17 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         halvings += (int)bc[5];
       }
       for (int a = tid; a < b.nb; a += NT) u[a] += alpha * (double)d[a];
-      cluster_barrier(cl, b.C);
+      sync_all<GRP>(cl, b.C, gs);
       if (dmax <= sp.newton_tol) { conv = true; break; }
     }
     int used = it > sp.newton_max ? sp.newton_max : it;
     newton_total += used;
     max_newton = used > max_newton ? used : max_newton;
-    if (!conv) { status = MLMC_ERR_NOT_CONVERGED; failed_step = step; break; }
+    if (!conv) {
+      status = GRP && s_abort ? MLMC_ERR_TIMEOUT : MLMC_ERR_NOT_CONVERGED;
+      failed_step = step;
+      break;
+    }
     for (int a = tid; a < b.nb; a += NT) {
       const int A = base + a;
       if (ta[A] < 0.0 && u[a] >= 0.5) {
@@ -676,18 +811,20 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       info[s] = o;
     }
   }
-  cl.sync();   // no CTA leaves while a neighbour may still read its shared memory
+  if (!GRP) cl.sync();   // no CTA leaves while a neighbour may still read its shared memory
 }
 
-template <typename KR, int DIM, bool GM, bool MG = false>
+template <typename KR, int DIM, bool GM, bool MG = false, bool GRP = false>
 inline cudaError_t set_attrs(const ClusterPlan& pl) {
-  auto kern = solve_cluster_kernel<KR, DIM, 512, 5, GM, MG>;
+  auto kern = solve_cluster_kernel<KR, DIM, 512, 5, GM, MG, GRP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-  if (e == cudaSuccess && pl.C > 8)
+  if (e == cudaSuccess && !GRP && pl.C > 8)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
+// Launch configuration: n clusters of C CTAs, or (group layout, pl.G > 0) a
+// plain grid of n groups of G CTAs.
 inline cudaLaunchConfig_t launch_cfg(const ClusterPlan& pl, int n, cudaStream_t st,
                                      cudaLaunchAttribute* at) {
   cudaLaunchConfig_t cfg = {};
@@ -696,27 +833,33 @@ inline cudaLaunchConfig_t launch_cfg(const ClusterPlan& pl, int n, cudaStream_t 
   cfg.dynamicSmemBytes = pl.smem;
   cfg.stream = st;
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = pl.C;
+  at[0].val.clusterDim.x = pl.G > 0 ? 1 : pl.C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pl.G > 0 ? 0 : 1;
   return cfg;
 }
 
-template <typename KR, int DIM, bool GM, bool MG>
+template <typename KR, int DIM, bool GM, bool MG, bool GRP = false>
 inline cudaError_t launch_one(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                               const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
                               double* slab, double* t_act, mlmc_sample_info* info,
                               unsigned long long* counters, const ClusterGlobal& g,
                               const MGDesc& mg, cudaStream_t st) {
-  cudaError_t e = set_attrs<KR, DIM, GM, MG>(pl);
+  cudaError_t e = set_attrs<KR, DIM, GM, MG, GRP>(pl);
   if (e != cudaSuccess) return e;
+  if (GRP) {
+    // tickets and barrier counters start from zero in every launch
+    e = cudaMemsetAsync(g.gsync, 0, group_sync_bytes(n), st);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t cfg = launch_cfg(pl, n, st, at);
-  return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<KR, DIM, 512, 5, GM, MG>, lv, ph, sp, coef64,
-                            coefK, pl.H, pl.coef_smem ? 1 : 0, slab, t_act, info, counters, g.u,
-                            g.F, (KR*)g.kr, g.code, mg, (KR*)g.mg);
+  return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<KR, DIM, 512, 5, GM, MG, GRP>, lv, ph, sp,
+                            coef64, coefK, pl.H, pl.coef_smem ? 1 : 0, slab, t_act, info, counters,
+                            g.u, g.F, (KR*)g.kr, g.code, mg, (KR*)g.mg, GRP ? pl.G : 0, g.gsync,
+                            g.gslot);
 }
 
 
