@@ -49,13 +49,14 @@ FLOP_NEWTON_NODE = 32
 # below any streamed-stencil traffic.
 TRAFFIC_2D_BYTES_PER_SOLVE_LAUNCH = 36.85e6
 # Algorithmic HBM bytes per node of the 3D global-memory sweep (couplings are
-# streamed from HBM every pass; 27 per node): an FP32 CG iteration reads 27
-# FP32 couplings and touches 14 FP32 vector words (164 B); an FP64 one 27 FP64
-# couplings and 14 FP64 words (328 B); a Newton iteration runs the residual and
-# the line-search passes, each 27 FP64 couplings and 8 FP64 words (2 x 280 B).
-BYTES_CG32_NODE_3D = 27 * 4 + 14 * 4
-BYTES_CG64_NODE_3D = 27 * 8 + 14 * 8
-BYTES_NEWTON_NODE_3D = 2 * (27 * 8 + 8 * 8)
+# streamed from HBM every pass, each symmetric pair stored once: 14 per node):
+# an FP32 CG iteration reads 14 FP32 couplings and touches 14 FP32 vector words
+# (112 B); an FP64 one 14 FP64 couplings and 14 FP64 words (224 B); a Newton
+# iteration runs the residual and the line-search passes, each 14 FP64
+# couplings and 8 FP64 words (2 x 176 B).
+BYTES_CG32_NODE_3D = 14 * 4 + 14 * 4
+BYTES_CG64_NODE_3D = 14 * 8 + 14 * 8
+BYTES_NEWTON_NODE_3D = 2 * (14 * 8 + 8 * 8)
 # iteration cap per time step on the 3D slab: its level 1 steps take up to
 # thousands of continuation iterations
 SLAB3D_NEWTON_MAX = 40000
@@ -394,7 +395,7 @@ def run_ours(args, w):
         "warmup": warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == B.MLMC_PREC_FP64 else
-                 "f64 nonlinear iteration/residual/QoI + f32 CG (f64 CG on the 32^2 level)",
+                 "f64 nonlinear iteration/residual/QoI + f32 CG (f64 KL field on the 32^2 level)",
         "data": "synthetic",
         "config": {"workload": w["name"], "N_l": w["N"], "grids": grids_of(w),
                    "steps_per_level": [w["m0"] * 2 ** l for l in range(w["levels"])],

@@ -90,7 +90,9 @@ typedef struct {
   int lin_max;           /* CG iterations per Newton step                            */
   int solver;            /* mlmc_solver: kernel layout of the per-sample sweep        */
   double mixed_cdr_max;  /* MLMC_PREC_MIXED uses FP32 inner solves only on levels with
-                            c dt max r' <= mixed_cdr_max (<= 0 selects the default 2) */
+                            c dt max r' <= mixed_cdr_max (<= 0 selects the default 2);
+                            the KL field is synthesised on the tensor cores on those
+                            of them with c dt max r' <= 2 */
   int cluster_size;      /* cluster layout: CTAs per sample (1, 2, 4, 8 or 16); 0 picks
                             the smallest that fits shared memory                        */
   int precond;           /* mlmc_precond: preconditioner of the CG inner solves          */
@@ -337,10 +339,11 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean
  * MLMC_LAYOUT_GROUP (3D grids) G CTAs per sample that are not a hardware
  * cluster -- an ordinary grid whose CTAs form groups of G in arrival order and
  * synchronise through bounded global-memory barriers (a wait that runs out,
- * after 180 s, fails the sample with MLMC_ERR_TIMEOUT) -- with G = min(S/n,
- * S/2, nodes/4096) for S resident CTAs on the device (nodes/512 when the
- * layout is set explicitly), so that a few samples of a large grid use every
- * SM instead of at most 16; a context runs its group
+ * after 180 s, fails the sample with MLMC_ERR_TIMEOUT) -- with G = k SMs / n
+ * for the largest k (CTAs per SM) that keeps G <= S/2 (S resident CTAs on the
+ * device) and at least 1024 nodes per CTA (512 when the layout is set
+ * explicitly), so that a few samples of a large grid use every SM, evenly,
+ * instead of at most 16; a context runs its group
  * launches one after another, and at most two may run at once on one device;
  * 0 automatic: the smallest shared-memory cluster that holds a sample, else
  * (3D) the group layout where G >= 32, else global-memory clusters of up to 16

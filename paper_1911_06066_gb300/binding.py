@@ -218,7 +218,7 @@ class State:
 
 
 def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, lin_rtol=1e-12,
-                lin_max=5000, levels=None, solver=MLMC_SOLVER_AUTO, mixed_cdr_max=0.0,
+                lin_max=5000, levels=None, solver=MLMC_SOLVER_AUTO, mixed_cdr_max=None,
                 cluster_size=0, precond=MLMC_PRECOND_JACOBI, mg_nu=0, mg_coarse_sweeps=0,
                 use_graph=False):
     """mlmc_config from a workload dictionary (see workloads.py).
@@ -246,7 +246,8 @@ def make_config(w, precision=MLMC_PREC_FP64, newton_tol=1e-12, newton_max=5000, 
     c.precision = precision
     c.newton_tol, c.newton_max, c.lin_rtol, c.lin_max = newton_tol, newton_max, lin_rtol, lin_max
     c.solver = solver
-    c.mixed_cdr_max = mixed_cdr_max
+    # the workload's own limit (key mixed_cdr_max) unless one is given
+    c.mixed_cdr_max = float(w.get("mixed_cdr_max", 0.0) if mixed_cdr_max is None else mixed_cdr_max)
     c.cluster_size = cluster_size
     c.precond, c.mg_nu, c.mg_coarse_sweeps = precond, mg_nu, mg_coarse_sweeps
     c.use_graph = 1 if use_graph else 0

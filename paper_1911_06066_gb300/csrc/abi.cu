@@ -42,10 +42,11 @@ mlmc_status mlmc::cuda_fail(mlmc_ctx* ctx, cudaError_t e, const char* where) {
 
 
 // --------------------------------------------------------------- workspace
-// FP32 inner solves are used only where the step Jacobian is at most mildly
-// indefinite: c dt max r' <= mixed_cdr_max (default 2), max r' =
-// c((1+a)^2/3 - a).  On strongly indefinite levels the negative-curvature
-// decisions of an FP32 CG can pick a different root than FP64.
+// FP32 inner solves are used only where c dt max r' <= mixed_cdr_max (default
+// 2), max r' = c((1+a)^2/3 - a).  On strongly indefinite levels the
+// continuation's FP32 pseudo-steps can end in a different root than FP64
+// ones (measured on the 3D 64x64x16 level at c dt max r' = 2.37; not on the
+// 2D 32^2 level at the same value, whose workload raises the limit).
 bool mlmc::level_mixed(const mlmc_config& c, const LevelDesc& lv) {
   if (c.precision != MLMC_PREC_MIXED) return false;
   double rmax = c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
@@ -455,12 +456,15 @@ extern "C" mlmc_status mlmc_kl_field_tc(mlmc_ctx* ctx, int level, const double* 
 
 // The KL field of the pipeline: on the tensor cores (split TF32) on levels
 // whose inner solves run in FP32 (MLMC_PREC_MIXED and c dt max r' <=
-// mixed_cdr_max), in FP64 elsewhere -- where the root selection is sensitive
-// to perturbations of the field, the field stays exact to FP64 rounding.
+// mixed_cdr_max) and whose steps are at most mildly indefinite (c dt max r'
+// <= 2), in FP64 elsewhere -- where the root selection is sensitive to
+// perturbations of the field, the field stays exact to FP64 rounding.
 // kws: kl_tc_workspace_bytes(M, n) bytes of the pair workspace.
 static mlmc_status kl_into(mlmc_ctx* ctx, int level, const double* xi, int n, double* Z,
                            char* kws, cudaStream_t st) {
-  if (level_mixed(ctx->cfg, ctx->lv[level]))
+  const mlmc_config& c = ctx->cfg;
+  const double cdr = ctx->lv[level].dt * c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a);
+  if (level_mixed(c, ctx->lv[level]) && cdr <= 2.0)
     return mlmc_kl_field_tc(ctx, level, xi, n, Z, kws, kl_tc_workspace_bytes(ctx->M, n), st);
   return mlmc_kl_field(ctx, level, xi, n, Z, st);
 }
@@ -480,14 +484,15 @@ static bool choose_plan(const mlmc_ctx* ctx, const LevelDesc& lv, bool mixed, in
   const int want = ctx->cfg.cluster_size ? ctx->cfg.cluster_size : ctx->tuned_C[level];
   if (want < 0 && ctx->cfg.solver == MLMC_SOLVER_AUTO) return false;
   bool ok = false;
-  if (want == MLMC_LAYOUT_GROUP) {
-    if (group_plan(lv, mixed, n, true, plan, &ok) == cudaSuccess && ok) return true;
+  MGDesc mg;
+  const bool gmg = level_gmg(ctx->cfg, lv, &mg);
+  if (want == MLMC_LAYOUT_GROUP) {   // (multigrid levels keep clusters)
+    if (!gmg && group_plan(lv, mixed, n, true, plan, &ok) == cudaSuccess && ok) return true;
     return cluster_plan(lv, mixed, 0, plan, true);
   }
   if (want > 100) return cluster_plan(lv, mixed, want - 100, plan, true);
   if (want > 0 && cluster_plan(lv, mixed, want, plan)) return true;
-  MGDesc mg;
-  if (want == 0 && level_gmg(ctx->cfg, lv, &mg)) return cluster_plan(lv, mixed, 0, plan, true);
+  if (want == 0 && gmg) return cluster_plan(lv, mixed, 0, plan, true);
   if (cluster_plan(lv, mixed, 0, plan)) return true;
   if (want == 0 && group_plan(lv, mixed, n, false, plan, &ok) == cudaSuccess && ok) return true;
   return cluster_plan(lv, mixed, 0, plan, true);
@@ -510,11 +515,16 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
   SolveWs w = solve_ws(ctx->cfg, lv, n, mixed);
   double* coef64 = (double*)(ws + w.coef64);
   float* coef32 = mixed ? (float*)(ws + w.coef32) : nullptr;
-  CK(ctx, launch_assemble(lv, ph, Z, n, coef64, coef32, st));
   ClusterPlan plan;
   const bool use_cluster = choose_plan(ctx, lv, mixed, level, n, &plan);
   if (ctx->cfg.solver == MLMC_SOLVER_CLUSTER && !use_cluster)
     return fail(ctx, MLMC_ERR_ARG, "cluster layout requested but no cluster plan fits");
+  MGDesc mg;
+  level_gmg(ctx->cfg, lv, &mg);
+  // the 3D global-memory sweeps (clusters and groups, Jacobi) read each
+  // symmetric coupling pair stored once
+  const bool sym = use_cluster && plan.gm && lv.dim == 3 && mg.G == 0;
+  CK(ctx, launch_assemble(lv, ph, Z, n, coef64, coef32, st, sym));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ctx->prof) {
     while (ctx->ev_pool.size() < ctx->ev_used + 2) {
@@ -536,8 +546,6 @@ static mlmc_status solve_into(mlmc_ctx* ctx, int level, const double* Z, int n, 
     g.F = (double*)(ws + w.F);
     g.kr = (void*)(ws + w.kr);
     g.code = (unsigned*)(ws + w.Ku);
-    MGDesc mg;
-    level_gmg(ctx->cfg, lv, &mg);
     g.mg = mg.G > 0 ? (void*)(ws + w.mg) : nullptr;
     if (plan.G > 0) {
       g.gsync = (unsigned*)(ws + w.grp);

@@ -12,7 +12,8 @@
 //            + Dxy (sx_a sy_b + sy_a sx_b) hz m1(az,bz) / 4 + (xz, yz analogues).
 // Each node gathers the rows of the 2^dim cells around it into its 3^dim
 // couplings, stored [sample][offset][node] (offset (dx,dy,dz) in {-1,0,1}^dim,
-// x fastest), so no two threads write the same entry.
+// x fastest), so no two threads write the same entry; or, for the 3D
+// global-memory sweeps (sym), only the offsets 13..26 (see launch_assemble).
 #include <math.h>
 
 #include "internal.cuh"
@@ -45,8 +46,9 @@ __device__ double element_entry(int dim, const double D[3][3], const double h[3]
 
 template <int DIM>
 __global__ void assemble_kernel(LevelDesc lv, Physics ph, const double* __restrict__ Z, int n,
-                                double* __restrict__ coef64, float* __restrict__ coef32) {
+                                double* __restrict__ coef64, float* __restrict__ coef32, int sym) {
   constexpr int NO = DIM == 3 ? 27 : (DIM == 2 ? 9 : 3);
+  constexpr int CTR = NO / 2;
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)n * lv.nodes) return;
   int s = (int)(g / lv.nodes);
@@ -90,27 +92,32 @@ __global__ void assemble_kernel(LevelDesc lv, Physics ph, const double* __restri
       }
   // stored times theta (1 implicit Euler, 1/2 Crank-Nicolson): the Hessian's
   // stiffness part, and with (1-theta)/theta the explicit part of the residual
-  int64_t base = (int64_t)s * NO * lv.nodes + A;
+  // with sym only the offsets CTR..NO-1 are stored, at CTR..NO-1 minus CTR
+  const int nst = sym ? NO - CTR : NO;
+  int64_t base = (int64_t)s * nst * lv.nodes + A;
 #pragma unroll
   for (int o = 0; o < NO; ++o) {
+    if (sym && o < CTR) continue;
+    const int oi = sym ? o - CTR : o;
     const double k = ph.theta * K[o];
-    coef64[base + (int64_t)o * lv.nodes] = k;
-    if (coef32) coef32[base + (int64_t)o * lv.nodes] = (float)k;
+    coef64[base + (int64_t)oi * lv.nodes] = k;
+    if (coef32) coef32[base + (int64_t)oi * lv.nodes] = (float)k;
   }
 }
 
 cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,
-                            double* coef64, float* coef32, cudaStream_t st) {
+                            double* coef64, float* coef32, cudaStream_t st, bool sym) {
   int64_t total = (int64_t)n * lv.nodes;
   if (total == 0) return cudaSuccess;
+  if (sym && lv.dim != 3) return cudaErrorInvalidValue;
   int bs = 128;
   unsigned grid = (unsigned)((total + bs - 1) / bs);
   if (lv.dim == 3)
-    assemble_kernel<3><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32);
+    assemble_kernel<3><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32, sym ? 1 : 0);
   else if (lv.dim == 2)
-    assemble_kernel<2><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32);
+    assemble_kernel<2><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32, 0);
   else
-    assemble_kernel<1><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32);
+    assemble_kernel<1><<<grid, bs, 0, st>>>(lv, ph, Z, n, coef64, coef32, 0);
   return cudaGetLastError();
 }
 

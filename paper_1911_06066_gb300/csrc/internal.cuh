@@ -220,8 +220,13 @@ cudaError_t launch_kl_field_tc(const LevelDesc& lv, int M, const double* sqrt_la
                                const float* phi_cells, const double* xi, int n, double* Z, void* ws,
                                unsigned long long* err, long long check_limit, cudaStream_t st);
 cudaError_t preload_kl_tc();
+// sym (3D only): store each symmetric pair once -- per sample [14][nodes], the
+// offsets 13..26 of {-1,0,1}^3 (centre first); the coupling to offset o < 13
+// is the neighbour's entry 26 - o (the global-memory sweeps of 3D grids).
+// The assembly is exactly symmetric (each pair sums the same cells in the same
+// order), so both layouts hold the same numbers.
 cudaError_t launch_assemble(const LevelDesc& lv, const Physics& ph, const double* Z, int n,
-                            double* coef64, float* coef32, cudaStream_t st);
+                            double* coef64, float* coef32, cudaStream_t st, bool sym = false);
 // Loads the assembly kernels' module (both dimensions) without launching.
 cudaError_t preload_assemble();
 cudaError_t launch_solve(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
@@ -260,14 +265,16 @@ struct ClusterGlobal {
   double* gslot = nullptr;     // group layout: group_slot_bytes(n, G)
 };
 bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm = false);
-// Group layout plan for n samples of the 3D grid lv: G CTAs per sample with
-// G = min(S / n, S / 2, GROUP_MAX_CTAS, nodes / 4096, GROUP_MAX_GRID / n), S
-// the device's resident-CTA capacity for the group kernel (force, the layout
-// requested by code: nodes / 512 instead of nodes / 4096).  *ok = false when
-// the layout does not apply: not 3D, n above GROUP_MAX_SAMPLES, or G below 32
-// (below 1 with force), where clusters of 16 CTAs serve as well.  G <= S / 2
-// keeps two group launches running at once (e.g. from two contexts) free of
-// deadlock: each waits at most for one incomplete group of its own.
+// Group layout plan for n samples of the 3D grid lv: G = k SMs / n CTAs per
+// sample for the largest k (CTAs per SM) with G <= S / 2 (S the device's
+// resident-CTA capacity for the group kernel), G <= GROUP_MAX_CTAS, n G <=
+// GROUP_MAX_GRID and at least 1024 nodes per CTA (512 with force, the layout
+// requested by code; where no such G exists it takes min(S / n, nodes / 512)).
+// *ok = false when the layout does not apply: not 3D, n
+// above GROUP_MAX_SAMPLES, or G below 32 (below 1 with force), where clusters
+// of 16 CTAs serve as well.  G <= S / 2 keeps two group launches running at
+// once (e.g. from two contexts) free of deadlock: each waits at most for one
+// incomplete group of its own.
 cudaError_t group_plan(const LevelDesc& lv, bool mixed, int n, bool force, ClusterPlan* plan, bool* ok);
 size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt);
 // Loads the kernel instance a plan launches and sets its attributes, so that

@@ -150,7 +150,11 @@ solve_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict
   for (int step = 1; step <= lv.m; ++step) {
     const double* up = sl ? sl + (int64_t)(step - 1) * N : ub + (int64_t)((step - 1) & 1) * N;
     double* u = sl ? sl + (int64_t)step * N : ub + (int64_t)(step & 1) * N;
-    for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) u[A] = up[A];
+    // start: u_{k-1}, or on levels with a unique root (no continuation) the
+    // linear extrapolation 2 u_{k-1} - u_{k-2}, which the root does not depend on
+    const double* upp = step < 2 || sp.flow ? nullptr
+                        : (sl ? sl + (int64_t)(step - 2) * N : u);   // u still holds u_{k-2}
+    for (int64_t A = threadIdx.x; A < N; A += SOLVE_THREADS) u[A] = upp ? 2.0 * up[A] - upp[A] : up[A];
     __syncthreads();
     const double c_up = (1.0 - ph.theta) / ph.theta;      // Crank-Nicolson: explicit part
     const double src_scale = stim_step_scale(ph, step, dt);

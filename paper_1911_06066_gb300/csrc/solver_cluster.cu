@@ -1,6 +1,8 @@
 // Host side of the cluster solver (solver_cluster.cuh): launch plans, kernel
 // attributes and the launches of the Jacobi-preconditioned instances; the
 // multigrid-preconditioned instances are compiled in solver_cluster_mg.cu.
+#include <algorithm>
+
 #include "solver_cluster.cuh"
 
 namespace mlmc {
@@ -79,44 +81,59 @@ static cudaError_t preload_one(const ClusterPlan& pl) {
   return pl.gm ? set_attrs<KR, DIM, true>(pl) : set_attrs<KR, DIM, false>(pl);
 }
 
-// Resident CTAs of the group kernel on the current device (per SM x SMs),
-// cached per device and precision: the first query loads the kernel, so it
-// runs before any graph capture (group_plan is called from the preloads).
+// Resident CTAs per SM of the group kernel and the SM count of the current
+// device, cached per device and precision: the first query loads the kernel,
+// so it runs before any graph capture (group_plan is called from the preloads).
 template <typename KR>
-static cudaError_t group_slots(size_t smem, int* S) {
-  static int cache[64] = {};
+static cudaError_t group_slots(size_t smem, int* per_sm, int* sms) {
+  static int cache[64][2] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < 64 && cache[dev] > 0) {
-    *S = cache[dev];
+  if (dev >= 0 && dev < 64 && cache[dev][0] > 0) {
+    *per_sm = cache[dev][0];
+    *sms = cache[dev][1];
     return cudaSuccess;
   }
-  int sms = 0, per = 0;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  int nsm = 0, per = 0;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   auto kern = solve_cluster_kernel<KR, 3, 512, 5, true, false, true>;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 512, smem)) != cudaSuccess) return e;
-  *S = per * sms;
-  if (dev >= 0 && dev < 64) cache[dev] = *S;
+  *per_sm = per;
+  *sms = nsm;
+  if (dev >= 0 && dev < 64) { cache[dev][0] = per; cache[dev][1] = nsm; }
   return cudaSuccess;
 }
 
+// G: the largest k * SMs / n (k = CTAs per SM, from the most the SMs hold
+// down to 1) that keeps G <= S / 2 and at least `min_nodes` nodes per CTA --
+// n G a whole multiple of the SM count, so that every SM runs the same number
+// of CTAs and no group waits for a CTA that shares its SM with more others.
 cudaError_t group_plan(const LevelDesc& lv, bool mixed, int n, bool force, ClusterPlan* plan, bool* ok) {
   *ok = false;
   if (lv.dim != 3 || n < 1 || n > GROUP_MAX_SAMPLES) return cudaSuccess;
   ClusterPlan pl;
   if (!cluster_plan(lv, mixed, 16, &pl, true)) return cudaSuccess;
-  int S = 0;
-  cudaError_t e = mixed ? group_slots<float>(pl.smem, &S) : group_slots<double>(pl.smem, &S);
+  int per = 0, sms = 0;
+  cudaError_t e = mixed ? group_slots<float>(pl.smem, &per, &sms) : group_slots<double>(pl.smem, &per, &sms);
   if (e != cudaSuccess) return e;
-  int G = S / n;
-  if (G > S / 2) G = S / 2;
-  if (G > GROUP_MAX_CTAS) G = GROUP_MAX_CTAS;
-  const int64_t per_cta = force ? 512 : 4096;   // nodes per CTA at least
-  if ((int64_t)G > lv.nodes / per_cta) G = (int)(lv.nodes / per_cta);
-  if ((int64_t)n * G > GROUP_MAX_GRID) G = GROUP_MAX_GRID / n;
+  const int S = per * sms;
+  const int64_t min_nodes = force ? 512 : 1024;   // nodes per CTA at least
+  int G = 0;
+  for (int k = per; k >= 1 && G == 0; --k) {
+    const int g = k * sms / n;
+    if (g >= 1 && g <= S / 2 && g <= GROUP_MAX_CTAS && (int64_t)n * g <= GROUP_MAX_GRID &&
+        lv.nodes / g >= min_nodes)
+      G = g;
+  }
+  if (G == 0 && force) {   // small grids: as many CTAs as the nodes allow
+    int64_t g = std::min<int64_t>(S / n, lv.nodes / min_nodes);
+    g = std::min<int64_t>(g, std::min<int64_t>(S / 2, GROUP_MAX_CTAS));
+    g = std::min<int64_t>(g, GROUP_MAX_GRID / n);
+    G = (int)g;
+  }
   if (G < (force ? 1 : 32)) return cudaSuccess;
   pl.C = G;
   pl.G = G;

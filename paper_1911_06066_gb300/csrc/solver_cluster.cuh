@@ -188,6 +188,19 @@ __device__ __forceinline__ void sync_all(cg::cluster_group& cl, int C, GroupSync
   else cluster_barrier(cl, C);
 }
 
+// Coupling o of node A from per-sample arrays with N nodes per offset.  SYM
+// (3D global-memory sweeps): each symmetric pair is stored once, offsets
+// 13..26 at 0..13, and offset o < 13 is the neighbour A + off(o)'s entry
+// 26 - o (at 13 - o); o is a constant after unrolling, so is the branch.
+template <bool SYM, int DIM, typename T>
+__device__ __forceinline__ T coupling(const T* c, int o, int64_t N, int A, int N0, int N01) {
+  constexpr int CTR = DIM == 3 ? 13 : (DIM == 2 ? 4 : 1);
+  if (!SYM) return c[(int64_t)o * N + A];
+  if (o >= CTR) return c[(int64_t)(o - CTR) * N + A];
+  const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+  return c[(int64_t)(CTR - o) * N + A + dx + dy * N0 + dz * N01];
+}
+
 // Deterministic cluster-wide sums (op 0) or maxima (op 1, of non-negative
 // values) of K values per thread.  Warps reduce by butterfly shuffles in TP
 // (float in the mixed CG, double otherwise); warp 0 combines the CTA's warps
@@ -321,7 +334,7 @@ __host__ __device__ inline SmemLayout smem_layout(int dim, int nmax, int kr, boo
   L.code = take((size_t)nmax * 4);
   L.red = take((size_t)4 * 32 * 8);
   L.slot = take((size_t)2 * 4 * 16 * 8);
-  L.bc = take(8 * 8);
+  L.bc = take(16 * 8);
   L.total = o;
   return L;
 }
@@ -406,10 +419,14 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   double* red = (double*)(smem + L.red);
   double* slot = (double*)(smem + L.slot);
   double* bc = (double*)(smem + L.bc);
+  KR* const bck = (KR*)(bc + 8);   // KR copies of broadcast scalars
   int par = 0;
 
-  const double* c64 = coef64 + (int64_t)s * NO * N;
-  const KR* cKg = coefK + (int64_t)s * NO * N;
+  // 3D global-memory sweeps read the couplings stored once per symmetric pair
+  constexpr bool SYM = GM && !MG && DIM == 3;
+  constexpr int NOS = SYM ? NO - CTR : NO;
+  const double* c64 = coef64 + (int64_t)s * NOS * N;
+  const KR* cKg = coefK + (int64_t)s * NOS * N;
   double* ta = t_act + (int64_t)s * N;
   double* sl = slab ? slab + (int64_t)s * (lv.m + 1) * N : nullptr;
   const double dt = lv.dt, inv_dt = 1.0 / lv.dt;
@@ -481,7 +498,11 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     // stencil of u_{k-1} (Crank-Nicolson), and the applied current's step average
     const double c_up = (1.0 - ph.theta) / ph.theta;
     const double src_scale = stim_step_scale(ph, step, dt);
-    for (int a = tid; a < b.nb; a += NT) u[a] = up[a];
+    // start: u_{k-1}, or on levels with a unique root (no continuation) the
+    // linear extrapolation 2 u_{k-1} - u_{k-2} (the buffer u still holds
+    // u_{k-2}), which the root does not depend on
+    const bool extrap = !sp.flow && step >= 2;
+    for (int a = tid; a < b.nb; a += NT) u[a] = extrap ? 2.0 * up[a] - u[a] : up[a];
     sync_all<GRP>(cl, b.C, gs);
     // On levels whose steps have several roots (sp.flow) the step follows the
     // gradient-flow continuation (see SolverParams).
@@ -511,7 +532,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       for (int a = tid; a < b.nb; a += NT) {
         const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
         const int A = base + a;
-        auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
+        auto c64A = [=](int o) { return coupling<SYM, DIM>(c64, o, N, A, b.N0, N01); };
         double ku = CFAST(c) ? stencil_fast<DIM, double>(u, a, b.N0, N01, c64A)
                              : stencil_band<DIM, GM, double>(b, uv, CI(c), CJ(c), CK_(c), c64A);
         if (c_up != 0.0)
@@ -529,7 +550,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         hm[a] = hmA;
         d[a] = (KR)0;
         const KR pvv = MG ? (KR)1 / (fabs(hmA) + mgb[mg.l[0].ks + A])   // l1-Jacobi (V-cycle smoother)
-                          : (KR)1 / fabs(hmA + (KR)c64[(int64_t)CTR * N + A]);
+                          : (KR)1 / fabs(hmA + (KR)c64[(int64_t)(SYM ? 0 : CTR) * N + A]);
         pinv[a] = pvv;
         if (SCALE) {
           f2_loc += f * f;
@@ -601,7 +622,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
               hs = CFAST(c) ? stencil_fast<DIM, KR>(sv, a, b.N0, N01, cf)
                             : stencil_band<DIM, GM, KR>(b, svv, CI(c), CJ(c), CK_(c), cf);
             } else {
-              auto cf = [=](int o) { return cKg[(int64_t)o * N + A]; };
+              auto cf = [=](int o) { return coupling<SYM, DIM>(cKg, o, N, A, b.N0, N01); };
               hs = CFAST(c) ? stencil_fast<DIM, KR>(sv, a, b.N0, N01, cf)
                             : stencil_band<DIM, GM, KR>(b, svv, CI(c), CJ(c), CK_(c), cf);
             }
@@ -623,18 +644,21 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
             KR v1[1] = {pq_loc};
             cluster_reduce<NT, KR, 1, GRP>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, gs, [=](double* o) {
               o[1] = o[0] > 0.0 ? (double)((KR)rzc / (KR)o[0]) : 0.0;
+              bck[0] = (KR)o[1];
+              bck[1] = o[0] <= 0.0 ? (KR)1 : (KR)0;
             });
           }
-          const double pq = bc[0];
           if (GRP && s_abort) break;
-          if (pq <= 0.0) {
+          // the scalars every thread needs, read in KR: no FP64 operation per
+          // thread and iteration (FP64 runs at 1/64 of the FP32 rate here)
+          if (bck[1] != (KR)0) {
             truncated = true;
             if (cgi == 1)
               for (int a = tid; a < b.nb; a += NT) d[a] = z[a];
             ok = true;
             break;
           }
-          const KR alpha = (KR)bc[1];
+          const KR alpha = bck[0];
           KR rzn_loc = 0;
           if (MG) {
             for (int a = tid; a < b.nb; a += NT) {
@@ -660,13 +684,14 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
             cluster_reduce<NT, KR, 1, GRP>(v1, 0, red, slot, bc, par, cl, b.C, b.rank, gs, [=](double* o) {
               o[1] = (double)((KR)o[0] / (KR)rzc);
               o[2] = o[0] <= rz_stop ? 1.0 : 0.0;
+              bck[2] = (KR)o[1];
+              bck[3] = (KR)o[2];
             });
           }
-          const double rz_new = bc[0];
           if (GRP && s_abort) break;
-          if (bc[2] != 0.0) { ok = true; break; }
-          beta_prev = (KR)bc[1];
-          rz = rz_new;
+          if (bck[3] != (KR)0) { ok = true; break; }
+          beta_prev = bck[2];
+          rz = bc[0];
         }
         if (!ok) { lin_fail = true; cgi = sp.lin_max; }
       }
@@ -725,24 +750,35 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         //   P3 = sum_i m_i r2(u_i) d_i^3 / 6,  P4 = sum_i m_i r3 d_i^4 / 24,
         // with r2 = r'' = c(2(1+a) - 6u) and r3 = r''' = -6c; one pass over the
         // nodes gives the four sums and thread 0 runs every Armijo test.
-        double v4[4] = {0.0, 0.0, 0.0, 0.0};
+        // The sums run in the inner solve's precision KR (FP32 on mixed
+        // levels): they only choose the step length, and the root that the
+        // Newton iteration converges to does not depend on it.  d.Hd takes
+        // the Hessian's diagonal mass term hm = m (1/dt - r'(u)) of this
+        // iteration (the shift is 0 outside the continuation).
+        KR v4[4] = {0, 0, 0, 0};
         for (int a = tid; a < b.nb; a += NT) {
           const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
           const int A = base + a;
-          auto c64A = [=](int o) { return c64[(int64_t)o * N + A]; };
-          const double kd = CFAST(c) ? stencil_fast<DIM, double>(d, a, b.N0, N01, c64A)
-                                     : stencil_band<DIM, GM, double>(b, dv, CI(c), CJ(c), CK_(c), c64A);
-          const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c));
-          const double uA = u[a], da = (double)d[a], d2 = da * da;
-          const double r1 = ph.c * (-3.0 * uA * uA + 2.0 * (1.0 + ph.a) * uA - ph.a);
-          const double r2 = ph.c * (2.0 * (1.0 + ph.a) - 6.0 * uA);
-          v4[0] += F[a] * da;
-          v4[1] += mA * (inv_dt - r1) * d2 + da * kd;
-          v4[2] += mA * r2 * d2 * da;
-          v4[3] += mA * d2 * d2;
+          KR kd;
+          if (!GM && coef_smem) {
+            auto cf = [=](int o) { return cs[o * nmax + a]; };
+            kd = CFAST(c) ? stencil_fast<DIM, KR>(d, a, b.N0, N01, cf)
+                          : stencil_band<DIM, GM, KR>(b, dv, CI(c), CJ(c), CK_(c), cf);
+          } else {
+            auto cf = [=](int o) { return coupling<SYM, DIM>(cKg, o, N, A, b.N0, N01); };
+            kd = CFAST(c) ? stencil_fast<DIM, KR>(d, a, b.N0, N01, cf)
+                          : stencil_band<DIM, GM, KR>(b, dv, CI(c), CJ(c), CK_(c), cf);
+          }
+          const KR mK = (KR)lumped_mass(lv, CI(c), CJ(c), CK_(c));
+          const KR uK = (KR)u[a], da = d[a], d2 = da * da;
+          const KR r2 = (KR)ph.c * ((KR)(2.0 * (1.0 + ph.a)) - (KR)6.0 * uK);
+          v4[0] += (KR)F[a] * da;
+          v4[1] += hm[a] * d2 + da * kd;
+          v4[2] += mK * r2 * d2 * da;
+          v4[3] += mK * d2 * d2;
         }
         const double alpha0 = alpha, cc = ph.c;   // alpha0 = 1
-        cluster_reduce<NT, double, 4, GRP>(v4, 0, red, slot, bc, par, cl, b.C, b.rank, gs,
+        cluster_reduce<NT, KR, 4, GRP>(v4, 0, red, slot, bc, par, cl, b.C, b.rank, gs,
                                       [=](double* o) {
                                         const double gd = o[0], dHd = o[1];
                                         const double P3 = o[2] / 6.0, P4 = -6.0 * cc * o[3] / 24.0;

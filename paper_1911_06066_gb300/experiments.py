@@ -111,3 +111,19 @@ def work_report(W_prime, N_l=None, ratio=16.0):
             "W_MLMC": float(np.sum(Wl * N_l)),
             "asymptotic": {"W_MC": 2.0 ** ((g + 4) * L), "W_MLMC": w_mlmc_asym(L),
                            "L": L}}
+
+
+if __name__ == "__main__":
+    # python -m paper_1911_06066_gb300.experiments [reps]: the full 1D+1
+    # controlled-convergence experiment on cuda:0, one JSON line
+    import json
+    import sys
+    import time
+
+    from . import binding as _B
+    from . import build as _build
+    _build.build()
+    t0 = time.perf_counter()
+    res = controlled_convergence_1d(_B, reps=int(sys.argv[1]) if len(sys.argv) > 1 else 4)
+    res["seconds"] = time.perf_counter() - t0
+    print(json.dumps(res))

@@ -50,16 +50,17 @@ def test_roofline_3d_bytes_and_fractions(bench, monkeypatch):
     peaks = {"fp64_tflops": 1.0, "fp32_tflops": 50.0}
     per = _per_level()
     lv = bench.add_hbm_bytes(bench.level_bounds(per, 1, peaks), per, 1)
-    nbytes = 164 * 1e9 + 328 * 2e8 + 560 * 1e8
+    nbytes = 112 * 1e9 + 224 * 2e8 + 352 * 1e8
     assert lv[0]["hbm_gb"] == pytest.approx(nbytes * 1e-9)
     r = bench.roofline_3d(lv, 1000.0, peaks)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 5000.0
     assert r["achieved"] == pytest.approx(nbytes / 0.4 / 1e9)
-    tot = nbytes + 328 * 1e8 + 560 * 1e7
+    tot = nbytes + 224 * 1e8 + 352 * 1e7
     assert r["aggregate_gbs"] == pytest.approx(tot / 1.0 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 5000.0)
-    assert bench.BYTES_CG32_NODE_3D == 27 * 4 + 14 * 4
-    assert bench.BYTES_NEWTON_NODE_3D == 2 * (27 * 8 + 8 * 8)
+    # each symmetric coupling pair stored once: 14 couplings per node
+    assert bench.BYTES_CG32_NODE_3D == 14 * 4 + 14 * 4
+    assert bench.BYTES_NEWTON_NODE_3D == 2 * (14 * 8 + 8 * 8)
 
 
 def test_measured_peak_lookup(bench, tmp_path, monkeypatch):

@@ -165,9 +165,10 @@ def test_solve_mixed_spd_level_fp32_inner(solver):
 
 
 def test_mixed_keeps_fp64_inner_solves_on_strongly_indefinite_levels():
-    """c dt max r' = 2.37 on the 32^2 level: the mixed configuration solves it
-    with FP64 CG, so its results equal the FP64 configuration's."""
-    w = W.MLMC2D_3LVL
+    """c dt max r' = 2.37 on the 32^2 level: with the default limit (2) the
+    mixed configuration solves it with FP64 CG, so its results equal the FP64
+    configuration's."""
+    w = dict(W.MLMC2D_3LVL, mixed_cdr_max=0.0)
     outs = []
     for prec in (B.MLMC_PREC_FP64, B.MLMC_PREC_MIXED):
         ctx = ctx_for(w, prec)
@@ -175,6 +176,21 @@ def test_mixed_keeps_fp64_inner_solves_on_strongly_indefinite_levels():
         t, _, info = ctx.solve(0, Z)
         outs.append((t.cpu().numpy(), info.cpu().numpy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_fp32_inner_solves_on_the_benchmark_32_level_reach_the_fp64_roots():
+    """The 2D benchmark workload raises the limit to 2.5: its 32^2 level
+    (c dt max r' = 2.37, the gradient-flow continuation) runs FP32 CG inside
+    the FP64 pseudo-steps and still ends every step in the FP64 root."""
+    w = W.MLMC2D_3LVL
+    outs = []
+    for prec in (B.MLMC_PREC_FP64, B.MLMC_PREC_MIXED):
+        ctx = ctx_for(w, prec)
+        Z = ctx.kl_field(0, ctx.xi(0, 0, torch.arange(128)))
+        t, _, info = ctx.solve(0, Z)
+        assert all(d["status"] == 0 for d in B.info_dicts(info))
+        outs.append(t.cpu().numpy())
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-6 * w["T"]
 
 
 def test_cluster_and_block_layouts_agree_full_size():
