@@ -485,12 +485,17 @@ def roofline_3d(levels, step_ms, peaks):
     dom = max(levels, key=lambda v: v["solve_ms"])
     achieved = dom["hbm_gb"] / (dom["solve_ms"] * 1e-3) if dom["solve_ms"] > 0 else 0.0
     tot_gb = sum(v["hbm_gb"] for v in levels)
+    # every level's fraction too: the finest grid is the one whose sweep
+    # streams its couplings from HBM (the coarser ones fit the L2)
+    for v in levels:
+        v["hbm_frac"] = v["hbm_gbs"] / peak if v.get("hbm_gbs") else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
             "kernel": "solve_cluster_kernel, global-memory layout (couplings streamed per pass), "
                       "grid level %d" % dom["level"],
             "peak_source": src, "aggregate_gbs": tot_gb / (step_ms * 1e-3) if step_ms > 0 else None,
-            "aggregate_frac": tot_gb / (step_ms * 1e-3) / peak if step_ms > 0 else None}
+            "aggregate_frac": tot_gb / (step_ms * 1e-3) / peak if step_ms > 0 else None,
+            "finest_level_frac": levels[-1].get("hbm_frac")}
 
 
 def add_hbm_bytes(levels, per_level, steps):

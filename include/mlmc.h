@@ -335,7 +335,9 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean
  * 4, 8, 16 a thread-block cluster of that many CTAs per sample with every
  * vector in shared memory (each CTA a band of whole rows; only where a band
  * fits); 100 + C (C = 1, 2, 4, 8, 16) a cluster of C CTAs per sample with the
- * vectors in global memory (each CTA a contiguous node range);
+ * vectors in global memory (the nodes dealt to the CTAs in chunks, cyclically);
+ * 300 + C (C = 1, 2, 4, 8, 16) the same with 256-thread CTAs (twice as many
+ * samples resident per SM);
  * MLMC_LAYOUT_GROUP (3D grids) G CTAs per sample that are not a hardware
  * cluster -- an ordinary grid whose CTAs form groups of G in arrival order and
  * synchronise through bounded global-memory barriers (a wait that runs out,
@@ -353,10 +355,10 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, double* mean, double* var, double* mean
  * level's layout for every later solve of this context.
  * ws: mlmc_workspace_bytes(ctx, level, n).  Outputs (host, may be NULL): best
  * (its code) and ms [MLMC_TUNE_CANDIDATES] in the order -1, 1, 2, 4, 8, 16,
- * 101, 102, 104, 108, 116, MLMC_LAYOUT_GROUP (-1 where a candidate was not
- * run).  Synchronises the stream.  A forced cfg.cluster_size still wins over
+ * 101, 102, 104, 108, 116, 301, 302, 304, 308, MLMC_LAYOUT_GROUP (-1 where a
+ * candidate was not run).  Synchronises the stream.  A forced cfg.cluster_size still wins over
  * the tuned value. */
-#define MLMC_TUNE_CANDIDATES 12
+#define MLMC_TUNE_CANDIDATES 16
 #define MLMC_LAYOUT_GROUP 200
 mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, const uint64_t* ids, int n,
                           void* ws, size_t ws_bytes, int* best, float* ms, void* stream);

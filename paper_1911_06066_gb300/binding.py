@@ -530,10 +530,11 @@ class Context:
         ids = torch.arange(first_id, first_id + n, dtype=torch.int64, device="cuda")
         ws = self.workspace(self.workspace_bytes(level, n), key="tune")
         best = C.c_int()
-        ms = np.zeros(12, np.float32)
+        ms = np.zeros(16, np.float32)
         self._check(lib().mlmc_autotune(self.h, level, seed, _p(ids), n, _p(ws), ws.numel(),
                                         C.byref(best), _dp(ms), _stream(stream)))
-        names = (-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116, MLMC_LAYOUT_GROUP)
+        names = (-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116, 301, 302, 304, 308,
+                 MLMC_LAYOUT_GROUP)
         return best.value, {k: float(v) for k, v in zip(names, ms) if v >= 0}
 
     def layout(self, level):

@@ -477,7 +477,7 @@ static mlmc_status kl_into(mlmc_ctx* ctx, int level, const double* xi, int n, do
 // cluster that holds a sample; else, on 3D grids, the group layout when it
 // gives a sample at least 32 CTAs; else global-memory clusters of 16), 1..16
 // shared-memory clusters of that size, 100 + C global-memory clusters of C
-// CTAs, MLMC_LAYOUT_GROUP the group layout.
+// CTAs (300 + C: of 256-thread CTAs), MLMC_LAYOUT_GROUP the group layout.
 static bool choose_plan(const mlmc_ctx* ctx, const LevelDesc& lv, bool mixed, int level, int n,
                         ClusterPlan* plan) {
   if (ctx->cfg.solver == MLMC_SOLVER_BLOCK) return false;
@@ -490,6 +490,7 @@ static bool choose_plan(const mlmc_ctx* ctx, const LevelDesc& lv, bool mixed, in
     if (!gmg && group_plan(lv, mixed, n, true, plan, &ok) == cudaSuccess && ok) return true;
     return cluster_plan(lv, mixed, 0, plan, true);
   }
+  if (want > 300) return cluster_plan(lv, mixed, want - 300, plan, true, 256);
   if (want > 100) return cluster_plan(lv, mixed, want - 100, plan, true);
   if (want > 0 && cluster_plan(lv, mixed, want, plan)) return true;
   if (want == 0 && gmg) return cluster_plan(lv, mixed, 0, plan, true);
@@ -499,7 +500,8 @@ static bool choose_plan(const mlmc_ctx* ctx, const LevelDesc& lv, bool mixed, in
 }
 
 static bool valid_layout(int C) {
-  const int ok[13] = {-1, 0, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116, MLMC_LAYOUT_GROUP};
+  const int ok[18] = {-1, 0, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116,
+                      301, 302, 304, 308, 316, MLMC_LAYOUT_GROUP};
   for (int v : ok)
     if (C == v) return true;
   return false;
@@ -610,7 +612,7 @@ extern "C" mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, co
   // candidates: the block kernel (only when the layout is not forced), shared-
   // memory clusters of 1..16 CTAs (where a band fits), global-memory clusters
   const int cand[MLMC_TUNE_CANDIDATES] = {-1, 1, 2, 4, 8, 16, 101, 102, 104, 108, 116,
-                                          MLMC_LAYOUT_GROUP};
+                                          301, 302, 304, 308, MLMC_LAYOUT_GROUP};
   float t_ms[MLMC_TUNE_CANDIDATES];
   int choice = 0;
   float best_ms = 0.f;
@@ -636,7 +638,8 @@ extern "C" mlmc_status mlmc_autotune(mlmc_ctx* ctx, int level, uint64_t seed, co
         bool gok = false;
         CK(ctx, group_plan(lv, mixed, n, true, &pl, &gok));
         if (!gok) continue;
-      } else if (!cluster_plan(lv, mixed, C > 100 ? C - 100 : C, &pl, C > 100)) {
+      } else if (!cluster_plan(lv, mixed, C > 300 ? C - 300 : (C > 100 ? C - 100 : C), &pl, C > 100,
+                               C > 300 ? 256 : 512)) {
         continue;
       }
       int active = 0;

@@ -264,7 +264,8 @@ struct ClusterGlobal {
   unsigned* gsync = nullptr;   // group layout: group_sync_bytes(n)
   double* gslot = nullptr;     // group layout: group_slot_bytes(n, G)
 };
-bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm = false);
+bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm = false,
+                  int nt = 512);
 // Group layout plan for n samples of the 3D grid lv: G = k SMs / n CTAs per
 // sample for the largest k (CTAs per SM) with G <= S / 2 (S the device's
 // resident-CTA capacity for the group kernel), G <= GROUP_MAX_CTAS, n G <=

@@ -22,8 +22,9 @@ size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt)
 // Launch plan: the smallest cluster whose bands fit the shared memory (or the
 // requested size want_C), and the block size.  Returns false when it does not
 // fit.  With gm the vectors live in global memory: any C works, and C = 0
-// picks clusters of 16 CTAs, or fewer for grids of at most 8192 nodes.
-bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm) {
+// picks clusters of 16 CTAs, or fewer for grids of at most 8192 nodes; nt is
+// the block size of the gm layout (512, or 256: twice the samples per SM).
+bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan, bool gm, int nt) {
   const int rowlen = lv.dim == 3 ? lv.N[0] * lv.N[1] : lv.N[0];
   const int nrows = lv.dim == 3 ? lv.N[2] : lv.N[1];   // 1 in one dimension: one row
   const size_t limit = 224 * 1024;
@@ -35,10 +36,10 @@ bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan
     }
     plan->C = C;
     plan->H = (int)((lv.nodes + C - 1) / C);
-    plan->nt = 512;
+    plan->nt = nt == 256 ? 256 : 512;
     plan->coef_smem = false;
     plan->gm = true;
-    plan->smem = smem_layout(lv.dim, 0, mixed ? 4 : 8, false, 512).total;
+    plan->smem = smem_layout(lv.dim, 0, mixed ? 4 : 8, false, plan->nt).total;
     return true;
   }
   for (int C = 1; C <= 16; C *= 2) {
@@ -68,6 +69,9 @@ static cudaError_t launch_nt(const LevelDesc& lv, const Physics& ph, const Solve
     return launch_one<KR, 3, true, false, true>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info,
                                                 counters, g, mg, st);
   }
+  if (pl.gm && pl.nt == 256)
+    return launch_one<KR, DIM, true, false, false, 256>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act,
+                                                        info, counters, g, mg, st);
   if (pl.gm)
     return launch_one<KR, DIM, true, false>(lv, ph, sp, pl, n, coef64, coefK, slab, t_act, info,
                                             counters, g, mg, st);
@@ -78,6 +82,7 @@ static cudaError_t launch_nt(const LevelDesc& lv, const Physics& ph, const Solve
 template <typename KR, int DIM>
 static cudaError_t preload_one(const ClusterPlan& pl) {
   if (pl.G > 0) return set_attrs<KR, 3, true, false, true>(pl);
+  if (pl.gm && pl.nt == 256) return set_attrs<KR, DIM, true, false, false, 256>(pl);
   return pl.gm ? set_attrs<KR, DIM, true>(pl) : set_attrs<KR, DIM, false>(pl);
 }
 
@@ -156,6 +161,8 @@ static cudaError_t max_clusters_one(const ClusterPlan& pl, int* count) {
     *count = per > 0 ? 1 : 0;
     return e;
   }
+  if (pl.gm && pl.nt == 256)
+    return cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 256, 5, true, false>, &cfg);
   return pl.gm ? cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, true, false>, &cfg)
                : cudaOccupancyMaxActiveClusters(count, solve_cluster_kernel<KR, DIM, 512, 5, false, false>, &cfg);
 }

@@ -344,7 +344,7 @@ __host__ __device__ inline SmemLayout smem_layout(int dim, int nmax, int kr, boo
 // phases spill a few words), which doubles the warps in flight on the CG
 // passes -- 1.5-1.8x faster on the 3D levels than one CTA with 128 registers.
 template <typename KR, int DIM, int NT, int NPT, bool GM, bool MG, bool GRP = false>
-__global__ void __launch_bounds__(NT, GM ? 2 : 1)
+__global__ void __launch_bounds__(NT, GM ? 1024 / NT : 1)
 solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __restrict__ coef64,
                      const KR* __restrict__ coefK, int H, int coef_smem, double* slab,
                      double* t_act, mlmc_sample_info* info, unsigned long long* counters,
@@ -384,10 +384,16 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   b.nrows = DIM == 3 ? b.N2 : b.N1;
   b.H = H;
   const int N = (int)lv.nodes;
+  // Global-memory layout with Jacobi (CYC): the nodes are dealt to the CTAs
+  // in chunks of NT, cyclically (CTA r takes chunks r, r + C, ...), so that
+  // every CTA gets the same share of boundary nodes -- with contiguous ranges
+  // the CTAs that own a whole boundary plane run the slower bounds-checked
+  // stencil on every node, and every barrier waits for them.
+  constexpr bool CYC = GM && !MG;
   if (GM) {
-    // H nodes per CTA, contiguous
-    b.base = min(b.rank * H, N);
-    b.nb = min(H, N - b.base);
+    // H nodes per CTA, contiguous (multigrid), or every node reachable (CYC)
+    b.base = CYC ? 0 : min(b.rank * H, N);
+    b.nb = CYC ? N : min(H, N - b.base);
     b.row0 = b.row1 = 0;
     b.nmax = H;
   } else {
@@ -398,6 +404,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     b.base = b.row0 * b.rowlen;
   }
   const int base = b.base;
+  // this thread's nodes a (A = base + a): a_first, a_first + a_step, ... < a_end
+  const int a_first = CYC ? b.rank * NT + (int)threadIdx.x : (int)threadIdx.x;
+  const int a_step = CYC ? b.C * NT : NT;
+  const int a_end = b.nb;
   const int nmax = b.nmax;
   const int N01 = b.N0 * b.N1;
   const int tid = threadIdx.x;
@@ -435,7 +445,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   // every neighbour lies inside the domain and inside this band (then the
   // stencil uses constant local offsets).
   unsigned* code = GM ? g_code + (int64_t)s * N + base : (unsigned*)(smem + L.code);
-  for (int a = tid; a < b.nb; a += NT) {
+  for (int a = a_first; a < a_end; a += a_step) {
     int i, j, k, row;
     if (GM) {
       const int A = base + a;
@@ -466,10 +476,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
 
   if (!GM && coef_smem)
     for (int o = 0; o < NO; ++o)
-      for (int a = tid; a < b.nb; a += NT) cs[o * nmax + a] = cKg[(int64_t)o * N + base + a];
+      for (int a = a_first; a < a_end; a += a_step) cs[o * nmax + a] = cKg[(int64_t)o * N + base + a];
   double sc[3];
   for (int dd = 0; dd < 3; ++dd) sc[dd] = ph.stim_ps ? ph.stim_ps[3 * s + dd] : ph.stim_c[dd];
-  for (int a = tid; a < b.nb; a += NT) {
+  for (int a = a_first; a < a_end; a += a_step) {
     const unsigned c = code[a];
     const int A = base + a;
     double x[3] = {CI(c) * lv.h[0], CJ(c) * lv.h[1], CK_(c) * lv.h[2]};
@@ -502,7 +512,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     // linear extrapolation 2 u_{k-1} - u_{k-2} (the buffer u still holds
     // u_{k-2}), which the root does not depend on
     const bool extrap = !sp.flow && step >= 2;
-    for (int a = tid; a < b.nb; a += NT) u[a] = extrap ? 2.0 * up[a] - u[a] : up[a];
+    for (int a = a_first; a < a_end; a += a_step) u[a] = extrap ? 2.0 * up[a] - u[a] : up[a];
     sync_all<GRP>(cl, b.C, gs);
     // On levels whose steps have several roots (sp.flow) the step follows the
     // gradient-flow continuation (see SolverParams).
@@ -529,7 +539,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       const bool SCALE = sizeof(KR) == 4 && sp.cg_scale != 0;
       double f2_loc = 0.0, f2p_loc = 0.0;
       KR rz_loc = 0;
-      for (int a = tid; a < b.nb; a += NT) {
+      for (int a = a_first; a < a_end; a += a_step) {
         const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
         const int A = base + a;
         auto c64A = [=](int o) { return coupling<SYM, DIM>(c64, o, N, A, b.N0, N01); };
@@ -571,7 +581,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         cluster_reduce<NT, double, 2, GRP>(v2, 0, red, slot, bc, par, cl, b.C, b.rank, gs, NoPost());
         if (bc[0] > 0.0) sigma = ldexp(1.0, -ilogb(sqrt(bc[0])));
         rz_scaled = bc[1] * sigma * sigma;
-        for (int a = tid; a < b.nb; a += NT) {
+        for (int a = a_first; a < a_end; a += a_step) {
           const KR rv = (KR)(-F[a] * sigma);
           r[a] = rv;
           if (!MG) {
@@ -586,7 +596,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         gmg::newton_setup<NT, DIM, KR>(mg, mgb, hm - base, cl, b.C, b.rank);
         gmg::vcycle<NT, DIM, KR>(mg, mgb, cKg, hm - base, pinv - base, r - base, z - base, cl, b.C,
                                  b.rank);
-        for (int a = tid; a < b.nb; a += NT) {
+        for (int a = a_first; a < a_end; a += a_step) {
           const KR zv = z[a];
           p[a] = zv;
           rz_loc += r[a] * zv;
@@ -613,7 +623,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           const bool first = cgi == 1;
           const KR* sv = first ? p : z;               // the vector the stencil reads
           const View<KR>& svv = first ? pv : zview;
-          for (int a = tid; a < b.nb; a += NT) {
+          for (int a = a_first; a < a_end; a += a_step) {
             const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
             const int A = base + a;
             KR hs;
@@ -654,23 +664,23 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           if (bck[1] != (KR)0) {
             truncated = true;
             if (cgi == 1)
-              for (int a = tid; a < b.nb; a += NT) d[a] = z[a];
+              for (int a = a_first; a < a_end; a += a_step) d[a] = z[a];
             ok = true;
             break;
           }
           const KR alpha = bck[0];
           KR rzn_loc = 0;
           if (MG) {
-            for (int a = tid; a < b.nb; a += NT) {
+            for (int a = a_first; a < a_end; a += a_step) {
               d[a] += alpha * p[a];
               r[a] = r[a] - alpha * q[a];
             }
             sync_all<GRP>(cl, b.C, gs);
             gmg::vcycle<NT, DIM, KR>(mg, mgb, cKg, hm - base, pinv - base, r - base, z - base, cl,
                                      b.C, b.rank);
-            for (int a = tid; a < b.nb; a += NT) rzn_loc += r[a] * z[a];
+            for (int a = a_first; a < a_end; a += a_step) rzn_loc += r[a] * z[a];
           } else {
-            for (int a = tid; a < b.nb; a += NT) {
+            for (int a = a_first; a < a_end; a += a_step) {
               d[a] += alpha * p[a];
               const KR rv = r[a] - alpha * q[a];
               const KR zv = pinv[a] * rv;
@@ -700,10 +710,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       if (lin_fail) break;
       if (SCALE && sigma != 1.0) {
         const KR inv_sigma = (KR)(1.0 / sigma);   // a power of two: exact
-        for (int a = tid; a < b.nb; a += NT) d[a] *= inv_sigma;
+        for (int a = a_first; a < a_end; a += a_step) d[a] *= inv_sigma;
       }
       KR dm_loc = 0;
-      for (int a = tid; a < b.nb; a += NT) dm_loc = fmax(dm_loc, fabs(d[a]));   // exact in KR
+      for (int a = a_first; a < a_end; a += a_step) dm_loc = fmax(dm_loc, fabs(d[a]));   // exact in KR
       {
         KR v1[1] = {dm_loc};
         cluster_reduce<NT, KR, 1, GRP>(v1, 1, red, slot, bc, par, cl, b.C, b.rank, gs, NoPost());
@@ -727,13 +737,13 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           // shortened to that move (a positive multiple keeps its sign along
           // every eigenvector of M/t + H); the next pseudo-step is shorter
           const double sc = FLOW_MOVE / dmax;
-          for (int a = tid; a < b.nb; a += NT) u[a] += sc * (double)d[a];
+          for (int a = a_first; a < a_end; a += a_step) u[a] += sc * (double)d[a];
           sync_all<GRP>(cl, b.C, gs);
           tau = t * 0.9 * sc;
           ++halvings;
           continue;
         }
-        for (int a = tid; a < b.nb; a += NT) u[a] += (double)d[a];
+        for (int a = a_first; a < a_end; a += a_step) u[a] += (double)d[a];
         sync_all<GRP>(cl, b.C, gs);
         if (dmax <= sp.newton_tol) { conv = true; break; }
         if (!newton_phase) {
@@ -756,7 +766,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         // the Hessian's diagonal mass term hm = m (1/dt - r'(u)) of this
         // iteration (the shift is 0 outside the continuation).
         KR v4[4] = {0, 0, 0, 0};
-        for (int a = tid; a < b.nb; a += NT) {
+        for (int a = a_first; a < a_end; a += a_step) {
           const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
           const int A = base + a;
           KR kd;
@@ -796,7 +806,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         alpha = bc[4];
         halvings += (int)bc[5];
       }
-      for (int a = tid; a < b.nb; a += NT) u[a] += alpha * (double)d[a];
+      for (int a = a_first; a < a_end; a += a_step) u[a] += alpha * (double)d[a];
       sync_all<GRP>(cl, b.C, gs);
       if (dmax <= sp.newton_tol) { conv = true; break; }
     }
@@ -808,7 +818,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
       failed_step = step;
       break;
     }
-    for (int a = tid; a < b.nb; a += NT) {
+    for (int a = a_first; a < a_end; a += a_step) {
       const int A = base + a;
       if (ta[A] < 0.0 && u[a] >= 0.5) {
         double uo = up[a];
@@ -825,7 +835,7 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
     // the quantity of interest: activation times (T where never reached), or
     // the final state u(T) (in the buffer of step m)
     const double* ufin = (lv.m & 1) ? ubuf1 : ubuf0;
-    for (int a = tid; a < b.nb; a += NT) {
+    for (int a = a_first; a < a_end; a += a_step) {
       if (ph.qoi == 1) ta[base + a] = ufin[a];
       else if (ta[base + a] < 0.0) ta[base + a] = lv.T;
     }
@@ -850,22 +860,22 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
   if (!GRP) cl.sync();   // no CTA leaves while a neighbour may still read its shared memory
 }
 
-template <typename KR, int DIM, bool GM, bool MG = false, bool GRP = false>
+template <typename KR, int DIM, bool GM, bool MG = false, bool GRP = false, int NT = 512>
 inline cudaError_t set_attrs(const ClusterPlan& pl) {
-  auto kern = solve_cluster_kernel<KR, DIM, 512, 5, GM, MG, GRP>;
+  auto kern = solve_cluster_kernel<KR, DIM, NT, 5, GM, MG, GRP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e == cudaSuccess && !GRP && pl.C > 8)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
-// Launch configuration: n clusters of C CTAs, or (group layout, pl.G > 0) a
-// plain grid of n groups of G CTAs.
+// Launch configuration: n clusters of C CTAs of pl.nt threads, or (group
+// layout, pl.G > 0) a plain grid of n groups of G CTAs.
 inline cudaLaunchConfig_t launch_cfg(const ClusterPlan& pl, int n, cudaStream_t st,
                                      cudaLaunchAttribute* at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n * pl.C));
-  cfg.blockDim = dim3(512);
+  cfg.blockDim = dim3((unsigned)pl.nt);
   cfg.dynamicSmemBytes = pl.smem;
   cfg.stream = st;
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -877,13 +887,14 @@ inline cudaLaunchConfig_t launch_cfg(const ClusterPlan& pl, int n, cudaStream_t 
   return cfg;
 }
 
-template <typename KR, int DIM, bool GM, bool MG, bool GRP = false>
+template <typename KR, int DIM, bool GM, bool MG, bool GRP = false, int NT = 512>
 inline cudaError_t launch_one(const LevelDesc& lv, const Physics& ph, const SolverParams& sp,
                               const ClusterPlan& pl, int n, const double* coef64, const KR* coefK,
                               double* slab, double* t_act, mlmc_sample_info* info,
                               unsigned long long* counters, const ClusterGlobal& g,
                               const MGDesc& mg, cudaStream_t st) {
-  cudaError_t e = set_attrs<KR, DIM, GM, MG, GRP>(pl);
+  if (pl.nt != NT) return cudaErrorInvalidValue;
+  cudaError_t e = set_attrs<KR, DIM, GM, MG, GRP, NT>(pl);
   if (e != cudaSuccess) return e;
   if (GRP) {
     // tickets and barrier counters start from zero in every launch
@@ -892,7 +903,7 @@ inline cudaError_t launch_one(const LevelDesc& lv, const Physics& ph, const Solv
   }
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t cfg = launch_cfg(pl, n, st, at);
-  return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<KR, DIM, 512, 5, GM, MG, GRP>, lv, ph, sp,
+  return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<KR, DIM, NT, 5, GM, MG, GRP>, lv, ph, sp,
                             coef64, coefK, pl.H, pl.coef_smem ? 1 : 0, slab, t_act, info, counters,
                             g.u, g.F, (KR*)g.kr, g.code, mg, (KR*)g.mg, GRP ? pl.G : 0, g.gsync,
                             g.gslot);

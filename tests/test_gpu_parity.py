@@ -36,10 +36,12 @@ def ctx_for(w, precision=B.MLMC_PREC_FP64, **kw):
 
 
 # solve layouts: the block-per-sample kernel, the automatic cluster layout
-# (shared memory where a band fits), and global-memory clusters of 16 and 2 CTAs
+# (shared memory where a band fits), global-memory clusters of 16 and 2 CTAs,
+# and global-memory clusters of 4 CTAs of 256 threads
 LAYOUTS = [pytest.param("block", id="block"), pytest.param("cluster", id="cluster"),
-           pytest.param("gm16", id="gm16"), pytest.param("gm2", id="gm2")]
-LAYOUT_CODE = {"gm16": 116, "gm2": 102}
+           pytest.param("gm16", id="gm16"), pytest.param("gm2", id="gm2"),
+           pytest.param("gm4x256", id="gm4x256")]
+LAYOUT_CODE = {"gm16": 116, "gm2": 102, "gm4x256": 304}
 
 
 def layout_ctx(w, layout, precision=B.MLMC_PREC_FP64, **kw):
