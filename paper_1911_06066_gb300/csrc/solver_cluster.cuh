@@ -201,6 +201,35 @@ __device__ __forceinline__ T coupling(const T* c, int o, int64_t N, int A, int N
   return c[(int64_t)(CTR - o) * N + A + dx + dy * N0 + dz * N01];
 }
 
+// The neighbour sum of the node with packed code c (i | j << 11 | k << 22,
+// bit 31: every neighbour inside the domain and the band).  Shared-memory
+// bands: the constant-offset sum or the band-aware one.  Global-memory layouts
+// (GM): one branch-free unrolled sum for every node, each offset predicated on
+// the neighbour lying inside the domain -- the same terms in the same order as
+// the other two, without a warp running both paths where its nodes straddle a
+// boundary.
+template <int DIM, bool GM, typename TA, typename TV, typename CF>
+__device__ __forceinline__ TA stencil_node(const Band& b, const TV* vloc, const View<TV>& v, int a,
+                                           unsigned c, int N01, CF cf) {
+  const int i = (int)(c & 2047u), j = (int)((c >> 11) & 2047u), k = (int)((c >> 22) & 511u);
+  if (!GM) {
+    return (c & 0x80000000u) ? stencil_fast<DIM, TA>(vloc, a, b.N0, N01, cf)
+                             : stencil_band<DIM, GM, TA>(b, v, i, j, k, cf);
+  }
+  const bool xl = i > 0, xh = i < b.N0 - 1;
+  const bool yl = DIM < 2 || j > 0, yh = DIM < 2 || j < b.N1 - 1;
+  const bool zl = DIM < 3 || k > 0, zh = DIM < 3 || k < b.N2 - 1;
+  TA y = 0;
+#pragma unroll
+  for (int o = 0; o < (DIM == 3 ? 27 : (DIM == 2 ? 9 : 3)); ++o) {
+    const int dx = o % 3 - 1, dy = (DIM >= 2 ? (o / 3) % 3 - 1 : 0), dz = DIM == 3 ? o / 9 - 1 : 0;
+    const bool in = (dx < 0 ? xl : (dx > 0 ? xh : true)) && (dy < 0 ? yl : (dy > 0 ? yh : true)) &&
+                    (dz < 0 ? zl : (dz > 0 ? zh : true));
+    if (in) y += (TA)cf(o) * (TA)vloc[a + dx + dy * b.N0 + dz * N01];
+  }
+  return y;
+}
+
 // Deterministic cluster-wide sums (op 0) or maxima (op 1, of non-negative
 // values) of K values per thread.  Warps reduce by butterfly shuffles in TP
 // (float in the mixed CG, double otherwise); warp 0 combines the CTA's warps
@@ -543,11 +572,9 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
         const int A = base + a;
         auto c64A = [=](int o) { return coupling<SYM, DIM>(c64, o, N, A, b.N0, N01); };
-        double ku = CFAST(c) ? stencil_fast<DIM, double>(u, a, b.N0, N01, c64A)
-                             : stencil_band<DIM, GM, double>(b, uv, CI(c), CJ(c), CK_(c), c64A);
+        double ku = stencil_node<DIM, GM, double>(b, u, uv, a, c, N01, c64A);
         if (c_up != 0.0)
-          ku += c_up * (CFAST(c) ? stencil_fast<DIM, double>(up, a, b.N0, N01, c64A)
-                                 : stencil_band<DIM, GM, double>(b, upv, CI(c), CJ(c), CK_(c), c64A));
+          ku += c_up * (stencil_node<DIM, GM, double>(b, up, upv, a, c, N01, c64A));
         const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c)), uA = u[a];
         double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
         if (src_scale != 0.0) f -= mA * src_scale * stim_shape(ph, lv, sc, CI(c), CJ(c), CK_(c));
@@ -629,12 +656,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
             KR hs;
             if (!GM && coef_smem) {
               auto cf = [=](int o) { return cs[o * nmax + a]; };
-              hs = CFAST(c) ? stencil_fast<DIM, KR>(sv, a, b.N0, N01, cf)
-                            : stencil_band<DIM, GM, KR>(b, svv, CI(c), CJ(c), CK_(c), cf);
+              hs = stencil_node<DIM, GM, KR>(b, sv, svv, a, c, N01, cf);
             } else {
               auto cf = [=](int o) { return coupling<SYM, DIM>(cKg, o, N, A, b.N0, N01); };
-              hs = CFAST(c) ? stencil_fast<DIM, KR>(sv, a, b.N0, N01, cf)
-                            : stencil_band<DIM, GM, KR>(b, svv, CI(c), CJ(c), CK_(c), cf);
+              hs = stencil_node<DIM, GM, KR>(b, sv, svv, a, c, N01, cf);
             }
             const KR sa = sv[a];
             KR pa, qv;
@@ -772,12 +797,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           KR kd;
           if (!GM && coef_smem) {
             auto cf = [=](int o) { return cs[o * nmax + a]; };
-            kd = CFAST(c) ? stencil_fast<DIM, KR>(d, a, b.N0, N01, cf)
-                          : stencil_band<DIM, GM, KR>(b, dv, CI(c), CJ(c), CK_(c), cf);
+            kd = stencil_node<DIM, GM, KR>(b, d, dv, a, c, N01, cf);
           } else {
             auto cf = [=](int o) { return coupling<SYM, DIM>(cKg, o, N, A, b.N0, N01); };
-            kd = CFAST(c) ? stencil_fast<DIM, KR>(d, a, b.N0, N01, cf)
-                          : stencil_band<DIM, GM, KR>(b, dv, CI(c), CJ(c), CK_(c), cf);
+            kd = stencil_node<DIM, GM, KR>(b, d, dv, a, c, N01, cf);
           }
           const KR mK = (KR)lumped_mass(lv, CI(c), CJ(c), CK_(c));
           const KR uK = (KR)u[a], da = d[a], d2 = da * da;
