@@ -374,7 +374,10 @@ mlmc_status mlmc_set_layout(mlmc_ctx* ctx, int level, int layout);
  * synchronises the stream).  Resets the running estimates first.  Levels run
  * concurrently on streams owned by the context (ordered after the work already
  * on `stream`; `stream` waits for them); within a level the fine and coarse
- * solves of a batch run concurrently.  ws: mlmc_run_workspace_bytes(ctx, N_l,
+ * solves of a batch run concurrently.  On a 3D level whose grids take the
+ * group layout (see mlmc_autotune) a batch holds at most as many samples as
+ * groups of >= 32 CTAs are resident at once (9 on a 152-SM device); the
+ * workspace size accounts for it.  ws: mlmc_run_workspace_bytes(ctx, N_l,
  * batch) bytes.
  * C_l (host [n_levels], may be NULL): the cost C_l of Sec. 3 per pair of level
  * l, in seconds: device time of the solve-kernel launches of its fine and

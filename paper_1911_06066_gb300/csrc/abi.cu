@@ -194,6 +194,13 @@ SolverParams mlmc::level_solver_params(const mlmc_config& c, const LevelDesc& lv
   sp.flow = level_has_several_roots(c.c, c.a, lv.dt) ? 1 : 0;
   sp.tau0 = 0.5 / (c.c * ((1.0 + c.a) * (1.0 + c.a) / 3.0 - c.a));
   sp.cg_scale = mixed && cg_needs_scaling(lv) ? 1 : 0;
+  // the predicated stencil pays where boundary nodes are many (measured: 3D
+  // 64x64x16, 17 % boundary nodes, 32.1 -> 24.6 s; the 2D levels) and costs
+  // where they are few (3D 128x128x32 and 256x256x64, 8.9 % and 4.6 %: 2.13 ->
+  // 2.62 s and 7.05 -> 10.05 s): 3D grids take it above 12 % boundary nodes
+  double interior = 1.0;
+  for (int d = 0; d < lv.dim; ++d) interior *= (double)(lv.N[d] - 2) / lv.N[d];
+  sp.pred_stencil = lv.dim < 3 || 1.0 - interior > 0.12 ? 1 : 0;
   return sp;
 }
 
@@ -830,9 +837,43 @@ static size_t level_run_ws(const mlmc_ctx* c, int l, int nb) {
 
 static int level_batch(int64_t N, int batch) { return (int)(N < batch ? (N > 0 ? N : 1) : batch); }
 
+// Samples per launch of level l's pairs inside mlmc_run: the whole batch,
+// except where a grid of the pair is a 3D grid that takes the group layout
+// automatically (no shared-memory cluster fits, no multigrid, layout 0 or the
+// group layout): there a launch holds at most as many samples as groups of
+// >= 32 CTAs fit the device at once.  Larger launches fall back to 16-CTA
+// clusters (measured slower: 64 samples of the 64x64x16 level took 354 s as
+// one cluster launch against ~34 s per 8 samples in groups); launches of this
+// size run one after another.
+static int level_cap(const mlmc_ctx* c, int l) {
+  int cap = 65535;
+  for (int g = l; g >= 0 && g >= l - 1; --g) {
+    const LevelDesc& lv = c->lv[g];
+    const int want = c->cfg.cluster_size ? c->cfg.cluster_size : c->tuned_C[g];
+    if (lv.dim != 3 || (want != 0 && want != MLMC_LAYOUT_GROUP) || c->cfg.solver == MLMC_SOLVER_BLOCK)
+      continue;
+    const bool mx = level_mixed(c->cfg, lv);
+    ClusterPlan pl;
+    MGDesc mg;
+    if (want == 0 && (cluster_plan(lv, mx, 0, &pl) || level_gmg(c->cfg, lv, &mg))) continue;
+    int m = 0;
+    if (group_resident_samples(lv, mx, &m) != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    if (m >= 1 && m < cap) cap = m;
+  }
+  return cap;
+}
+
+static int level_batch(const mlmc_ctx* c, int l, int64_t N, int batch) {
+  const int cap = level_cap(c, l);
+  return level_batch(N, batch < cap ? batch : cap);
+}
+
 static size_t run_ws(const mlmc_ctx* c, const int64_t* N_l, int batch) {
   size_t s = 0;
-  for (int l = 0; l < c->cfg.n_levels; ++l) s += level_run_ws(c, l, level_batch(N_l[l], batch));
+  for (int l = 0; l < c->cfg.n_levels; ++l) s += level_run_ws(c, l, level_batch(c, l, N_l[l], batch));
   return s;
 }
 
@@ -873,7 +914,7 @@ static mlmc_status run_levels(mlmc_ctx* ctx, const int64_t* first_id, const int6
         const LevelDesc& d = ctx->lv[lv];
         const bool mx = level_mixed(ctx->cfg, d);
         ClusterPlan pl;
-        if (choose_plan(ctx, d, mx, lv, level_batch(count[l], batch), &pl))
+        if (choose_plan(ctx, d, mx, lv, level_batch(ctx, l, count[l], batch), &pl))
           CK(ctx, preload_solve_cluster(d, mx, pl));
         else
           CK(ctx, preload_solve(d, mx));
@@ -941,7 +982,7 @@ static mlmc_status enqueue_levels(mlmc_ctx* ctx, const int64_t* first_id, const 
   char* p = ws;
   for (int l = 0; l < L; ++l) {
     cudaStream_t sf = ctx->lvl_stream[2 * l], sc = ctx->lvl_stream[2 * l + 1];
-    const int nbl = level_batch(count[l], batch);
+    const int nbl = level_batch(ctx, l, count[l], batch);
     char* q = p;
     uint64_t* ids = (uint64_t*)q; q += align256((size_t)nbl * 8);
     double* y = (double*)q; q += align256((size_t)nbl * ctx->lv[0].nodes * 8);

@@ -65,6 +65,9 @@ struct SolverParams {
                          // gradient-flow continuation instead of Newton-CG
   double tau0;           // first pseudo-step of the continuation, 1 / (2 max r')
   int cg_scale;          // FP32 CG: solve for a power-of-two scaled right-hand side
+  int pred_stencil = 1;       // global-memory layouts: the predicated branch-free stencil
+                              // for every node (1), or the constant-offset stencil for
+                              // interior nodes and the bounds-checked one at the boundary
   long long grp_check = -1;   // >= 0: check of the group layout's bounded waits -- the
                               // first barrier waits for one arrival too many, at most
                               // grp_check polls, and the sample ends with MLMC_ERR_TIMEOUT
@@ -277,6 +280,9 @@ bool cluster_plan(const LevelDesc& lv, bool mixed, int want_C, ClusterPlan* plan
 // once (e.g. from two contexts) free of deadlock: each waits at most for one
 // incomplete group of its own.
 cudaError_t group_plan(const LevelDesc& lv, bool mixed, int n, bool force, ClusterPlan* plan, bool* ok);
+// Samples of the 3D grid lv whose groups of at least 32 CTAs are resident at
+// once (resident CTAs / 32; 0 when lv is not 3D).
+cudaError_t group_resident_samples(const LevelDesc& lv, bool mixed, int* m);
 size_t cluster_smem_bytes(int dim, int nmax, bool mixed, bool coef_smem, int nt);
 // Loads the kernel instance a plan launches and sets its attributes, so that
 // a timed launch does not include module loading.

@@ -116,6 +116,17 @@ static cudaError_t group_slots(size_t smem, int* per_sm, int* sms) {
 // down to 1) that keeps G <= S / 2 and at least `min_nodes` nodes per CTA --
 // n G a whole multiple of the SM count, so that every SM runs the same number
 // of CTAs and no group waits for a CTA that shares its SM with more others.
+cudaError_t group_resident_samples(const LevelDesc& lv, bool mixed, int* m) {
+  *m = 0;
+  ClusterPlan pl;
+  if (lv.dim != 3 || !cluster_plan(lv, mixed, 16, &pl, true)) return cudaSuccess;
+  int per = 0, sms = 0;
+  cudaError_t e = mixed ? group_slots<float>(pl.smem, &per, &sms) : group_slots<double>(pl.smem, &per, &sms);
+  if (e != cudaSuccess) return e;
+  *m = per * sms / 32;
+  return cudaSuccess;
+}
+
 cudaError_t group_plan(const LevelDesc& lv, bool mixed, int n, bool force, ClusterPlan* plan, bool* ok) {
   *ok = false;
   if (lv.dim != 3 || n < 1 || n > GROUP_MAX_SAMPLES) return cudaSuccess;

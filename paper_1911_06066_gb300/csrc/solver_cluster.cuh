@@ -204,15 +204,15 @@ __device__ __forceinline__ T coupling(const T* c, int o, int64_t N, int A, int N
 // The neighbour sum of the node with packed code c (i | j << 11 | k << 22,
 // bit 31: every neighbour inside the domain and the band).  Shared-memory
 // bands: the constant-offset sum or the band-aware one.  Global-memory layouts
-// (GM): one branch-free unrolled sum for every node, each offset predicated on
-// the neighbour lying inside the domain -- the same terms in the same order as
-// the other two, without a warp running both paths where its nodes straddle a
-// boundary.
+// (GM, pred): one branch-free unrolled sum for every node, each offset
+// predicated on the neighbour lying inside the domain -- the same terms in the
+// same order as the other two, without a warp running both paths where its
+// nodes straddle a boundary (chosen per level: SolverParams::pred_stencil).
 template <int DIM, bool GM, typename TA, typename TV, typename CF>
 __device__ __forceinline__ TA stencil_node(const Band& b, const TV* vloc, const View<TV>& v, int a,
-                                           unsigned c, int N01, CF cf) {
+                                           unsigned c, int N01, CF cf, int pred) {
   const int i = (int)(c & 2047u), j = (int)((c >> 11) & 2047u), k = (int)((c >> 22) & 511u);
-  if (!GM) {
+  if (!GM || !pred) {
     return (c & 0x80000000u) ? stencil_fast<DIM, TA>(vloc, a, b.N0, N01, cf)
                              : stencil_band<DIM, GM, TA>(b, v, i, j, k, cf);
   }
@@ -572,9 +572,9 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
         const unsigned c = GM ? gm_code<DIM>(b, base + a) : code[a];
         const int A = base + a;
         auto c64A = [=](int o) { return coupling<SYM, DIM>(c64, o, N, A, b.N0, N01); };
-        double ku = stencil_node<DIM, GM, double>(b, u, uv, a, c, N01, c64A);
+        double ku = stencil_node<DIM, GM, double>(b, u, uv, a, c, N01, c64A, sp.pred_stencil);
         if (c_up != 0.0)
-          ku += c_up * (stencil_node<DIM, GM, double>(b, up, upv, a, c, N01, c64A));
+          ku += c_up * (stencil_node<DIM, GM, double>(b, up, upv, a, c, N01, c64A, sp.pred_stencil));
         const double mA = lumped_mass(lv, CI(c), CJ(c), CK_(c)), uA = u[a];
         double f = ku + mA * inv_dt * (uA - up[a]) - mA * rxn(ph, uA);
         if (src_scale != 0.0) f -= mA * src_scale * stim_shape(ph, lv, sc, CI(c), CJ(c), CK_(c));
@@ -656,10 +656,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
             KR hs;
             if (!GM && coef_smem) {
               auto cf = [=](int o) { return cs[o * nmax + a]; };
-              hs = stencil_node<DIM, GM, KR>(b, sv, svv, a, c, N01, cf);
+              hs = stencil_node<DIM, GM, KR>(b, sv, svv, a, c, N01, cf, sp.pred_stencil);
             } else {
               auto cf = [=](int o) { return coupling<SYM, DIM>(cKg, o, N, A, b.N0, N01); };
-              hs = stencil_node<DIM, GM, KR>(b, sv, svv, a, c, N01, cf);
+              hs = stencil_node<DIM, GM, KR>(b, sv, svv, a, c, N01, cf, sp.pred_stencil);
             }
             const KR sa = sv[a];
             KR pa, qv;
@@ -797,10 +797,10 @@ solve_cluster_kernel(LevelDesc lv, Physics ph, SolverParams sp, const double* __
           KR kd;
           if (!GM && coef_smem) {
             auto cf = [=](int o) { return cs[o * nmax + a]; };
-            kd = stencil_node<DIM, GM, KR>(b, d, dv, a, c, N01, cf);
+            kd = stencil_node<DIM, GM, KR>(b, d, dv, a, c, N01, cf, sp.pred_stencil);
           } else {
             auto cf = [=](int o) { return coupling<SYM, DIM>(cKg, o, N, A, b.N0, N01); };
-            kd = stencil_node<DIM, GM, KR>(b, d, dv, a, c, N01, cf);
+            kd = stencil_node<DIM, GM, KR>(b, d, dv, a, c, N01, cf, sp.pred_stencil);
           }
           const KR mK = (KR)lumped_mass(lv, CI(c), CJ(c), CK_(c));
           const KR uK = (KR)u[a], da = d[a], d2 = da * da;

@@ -145,3 +145,23 @@ def test_level1_full_run_every_step_a_root_in_both_layouts():
         _, rmax = ctx.slab_residual(1, Z, slab, full=False)
         assert rmax.item() <= 1e-8, rmax.item()
         ctx.close()
+
+
+def test_capped_group_launches_inside_an_estimate():
+    """20 samples of the 64x64x16 level in one estimate: the group layout
+    caps a launch at the samples whose groups of >= 32 CTAs are resident at
+    once (9 on GB300), so the level runs as several group launches one after
+    another; the mean equals that of one 16-CTA cluster launch."""
+    w = short_slab(4)
+    st = torch.cuda.Stream()
+    means = {}
+    for layout in (0, 116):
+        ctx = B.Context(B.make_config(w, B.MLMC_PREC_FP64, use_graph=True))
+        for l in range(2):
+            ctx.set_layout(l, layout)
+        with torch.cuda.stream(st):
+            r = ctx.run([4, 20], seed=6, batch=64, stream=st)
+        assert r["stats"]["failed"] == 0
+        means[layout] = r["mean"]
+        ctx.close()
+    assert np.abs(means[0] - means[116]).max() <= 1e-6 * w["T"]
