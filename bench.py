@@ -42,12 +42,6 @@ METRIC = "time-to-RMSE eps (s) for MLMC mean activation map; stencil HBM GB/s; p
 # precision and in FP64 respectively.
 FLOP_CG_NODE = 31
 FLOP_NEWTON_NODE = 32
-# DRAM bytes (read + write) per solve launch of one estimate of the 3-level 2D
-# workload, mean over its 5 launches: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the timed estimate (automatic layouts; 184 MB per
-# estimate).  The sweep keeps each sample's state on chip, so this is far
-# below any streamed-stencil traffic.
-TRAFFIC_2D_BYTES_PER_SOLVE_LAUNCH = 36.85e6
 # Algorithmic HBM bytes per node of the 3D global-memory sweep (couplings are
 # streamed from HBM every pass, each symmetric pair stored once: 14 per node):
 # an FP32 CG iteration reads 14 FP32 couplings and touches 14 FP32 vector words
@@ -458,7 +452,8 @@ def roofline_2d(levels, step_ms, peaks, auto_layouts):
     tot_bound = sum(v["alu_bound_ms"] for v in levels)
     return {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s",
             "frac": achieved / p64,
-            # measured with the automatic layouts only, and on the earlier sweep
+            # no DRAM capture of the current sweep at this size: the samples live
+            # on chip (shared memory / L2), see the 2D profile summary
             "traffic": None,
             "kernel": "solve_cluster_kernel (per-sample sweep), grid level %d: FP64 + FP32 work "
                       "as FP64-equivalent flops" % dom["level"],
