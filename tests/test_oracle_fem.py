@@ -153,3 +153,30 @@ def test_spatial_convergence_rate_against_the_heat_equation(dim, ns):
     ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
     assert all(3.8 < r < 4.2 for r in ratios[1:]), (errs, ratios)
     assert 3.5 < ratios[0] < 4.5, (errs, ratios)
+
+
+@pytest.mark.parametrize("dim,n", [(2, (6, 5)), (3, (4, 3, 3))])
+def test_each_coupling_pair_is_symmetric_and_out_of_domain_couplings_are_zero(dim, n):
+    """The coupling of node A to offset o equals the coupling of node A + o to
+    offset -o (to rounding: the quadrature here multiplies the gradient
+    factors of (a, b) and (b, a) in different orders), and an offset that
+    leaves the domain carries exactly zero -- the two facts that let the 3D
+    global-memory sweeps store each pair once and read the partner's entry."""
+    rng = np.random.default_rng(11)
+    L = [1.0, 0.7, 0.4][:dim]
+    lv = level(dim, n, s_t=2.5e-4, s_l0=1e-3, th0=30.0, th1=-45.0, L=L)
+    _, kst = O.assemble(lv, rng.normal(0, 0.4, lv.cells))
+    NO = 3 ** dim
+    K = kst.reshape(lv.nodes, NO)
+    N = [n[d] + 1 for d in range(dim)] + [1] * (3 - dim)
+    for A in range(lv.nodes):
+        i, j, k = A % N[0], (A // N[0]) % N[1], A // (N[0] * N[1])
+        for o in range(NO):
+            dx, dy, dz = o % 3 - 1, (o // 3) % 3 - 1 if dim >= 2 else 0, o // 9 - 1 if dim == 3 else 0
+            ii, jj, kk = i + dx, j + dy, k + dz
+            if not (0 <= ii < N[0] and 0 <= jj < N[1] and 0 <= kk < N[2]):
+                assert K[A, o] == 0.0
+                continue
+            B = (kk * N[1] + jj) * N[0] + ii
+            # rounding of sums of terms of both signs: against the row's scale
+            assert abs(K[A, o] - K[B, NO - 1 - o]) <= 1e-15 * np.abs(K[A]).max(), (A, o)
