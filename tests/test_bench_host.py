@@ -58,6 +58,9 @@ def test_roofline_3d_bytes_and_fractions(bench, monkeypatch):
     tot = nbytes + 224 * 1e8 + 352 * 1e7
     assert r["aggregate_gbs"] == pytest.approx(tot / 1.0 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 5000.0)
+    # every level carries its own fraction; the finest level's is reported too
+    assert [v["hbm_frac"] for v in lv] == pytest.approx([v["hbm_gbs"] / 5000.0 for v in lv])
+    assert r["finest_level_frac"] == pytest.approx(lv[-1]["hbm_gbs"] / 5000.0)
     # each symmetric coupling pair stored once: 14 couplings per node
     assert bench.BYTES_CG32_NODE_3D == 14 * 4 + 14 * 4
     assert bench.BYTES_NEWTON_NODE_3D == 2 * (14 * 8 + 8 * 8)
